@@ -1,0 +1,314 @@
+"""Benchmark of the phase-parallel Dijkstra hot path on one GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload 1..5] [--impl ours|reference]
+
+A step is one pass of the whole hot path over the workload: for a single-graph
+workload one solve (threshold reduce, selection, relaxation in every phase, until
+F is empty) from the workload's source (sources rotate for multi-source
+workloads); for the batched workload one launch of all its solves.  Graph
+preprocessing is timed once and reported separately (``prep_ms``); the
+end-to-end number (``e2e``) includes it, together with the host->device copy of
+the CSR graph from pinned memory and the device->host read of the distances.
+
+Metric: GTEPS = (sum over solves of the out-degrees of the settled vertices,
+i.e. every edge relaxed once) / solve time.  Phases and queries/s are reported
+alongside.  Rank 0 prints one JSON line.
+
+Under torchrun (N>1) every rank runs an independent replica of the workload (the
+method has no exchange step on one GPU), value = all ranks' edges / max time.
+``--impl reference`` times the CPU oracle's binary-heap Dijkstra instead (rank 0
+only) on the same workload and metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SSSP GTEPS & phases (learned/batched vs plain IN+OUT, 1 GB300); queries/s"
+L2_BYTES = 129 * 2**20
+DEFAULT_WORKLOAD = 2  # the 1024x1024 grid: the second workload of the study
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", type=int, default=DEFAULT_WORKLOAD)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--criterion", default="in_out", choices=["in_out", "simple", "learned"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait(timeout=5)
+            self.f.close()
+
+    def summary(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def build_workload(k: int):
+    import graphgen as gg
+    return gg.workload(k)
+
+
+def crit_value(sp, name):
+    return {"in_out": sp.IN_OUT, "simple": sp.SIMPLE, "learned": sp.IN_OUT | sp.POLICY_LEARNED}[name]
+
+
+def run_reference(args, wl):
+    """CPU oracle (binary-heap Dijkstra, one host core) on the same workload."""
+    import oracle
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    solves = wl.solves
+    times, edges = [], 0
+    for step in range(args.warmup + args.steps):
+        gi, s = solves[step % len(solves)]
+        g = wl.graphs[gi]
+        t0 = time.perf_counter()
+        d = oracle.dijkstra(g, s)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(dt)
+            edges += int(g.outdeg()[d != oracle.INF].sum())
+    total = sum(times)
+    value = edges / total / 1e9
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": wl.name, "solver": "oracle binary-heap Dijkstra, 1 host core"},
+        "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} whole solves of {wl.name}"},
+        "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def cpu_baseline(wl, budget_s=12.0):
+    """Oracle Dijkstra on the host: whole solves until ~budget_s of CPU time."""
+    import oracle
+    edges, t, count = 0, 0.0, 0
+    while t < budget_s and count < 64:
+        gi, s = wl.solves[count % len(wl.solves)]
+        g = wl.graphs[gi]
+        t0 = time.perf_counter()
+        d = oracle.dijkstra(g, s)
+        t += time.perf_counter() - t0
+        edges += int(g.outdeg()[d != oracle.INF].sum())
+        count += 1
+    return {"value": edges / t / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+            "sample": f"{count} whole binary-heap Dijkstra solves of {wl.name} ({t:.1f} s, 1 thread)"}
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    wl = build_workload(args.workload)
+    if args.impl == "reference":
+        run_reference(args, wl)
+        return
+
+    import torch
+    import paper_1903_12085_gb300 as sp
+
+    torch.cuda.set_device(local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+    crit = crit_value(sp, args.criterion)
+    stream = torch.cuda.current_stream()
+    hbm, peak_kind = peaks()
+
+    # ---- device-resident graphs (prep timed once)
+    t0 = time.perf_counter()
+    G = [sp.Graph.from_csr(g, reverse=(args.criterion != "in_out")) for g in wl.graphs]
+    torch.cuda.synchronize()
+    prep_ms = 1e3 * (time.perf_counter() - t0)
+    batched = args.workload == 4
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda")
+
+    if batched:
+        B = sp.Batch([G[i] for i, _ in wl.solves], [s for _, s in wl.solves], crit)
+        edges_per_step = None
+
+        def step(k):
+            B.launch()
+    else:
+        outs = [torch.empty(g.n, dtype=torch.int64, device="cuda") for g in wl.graphs]
+
+        def step(k):
+            gi, s = wl.solves[k % len(wl.solves)]
+            return sp.solve_trace(G[gi], s, crit, out=outs[gi], settle=False)
+
+    # edges / phases / frontier work per step (deterministic: from one traced pass per solve)
+    per_solve = []
+    for k in range(len(wl.solves)):
+        gi, s = wl.solves[k]
+        _, stats, _, _ = sp.solve_trace(G[gi], s, crit, settle=False)
+        per_solve.append(stats)
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    edges = phases = settled = sum_f = 0
+    nsolves = 0
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush.zero_()  # L2 flush between timed steps (outside the events)
+            ev[k][0].record(stream)
+            step(k)
+            ev[k][1].record(stream)
+            if batched:
+                for st in per_solve:
+                    edges += st["edges_relaxed"]; phases += st["phases"]
+                    settled += st["settled"]; sum_f += st["sum_frontier"]
+                nsolves += len(per_solve)
+            else:
+                st = per_solve[k % len(per_solve)]
+                edges += st["edges_relaxed"]; phases += st["phases"]
+                settled += st["settled"]; sum_f += st["sum_frontier"]
+                nsolves += 1
+        torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if pg:
+        t = torch.tensor([total_ms], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        total_ms = float(t.item())
+        pg.barrier()
+    value = ws * edges / (total_ms * 1e-3) / 1e9
+    kernel_ms = total_ms / args.steps
+
+    # roofline of the solve kernel: algorithmic bytes per launch / launch time
+    # per solve: 16 B per relaxed edge (8 B edge + 8 B distance word) + 16 B per
+    # settled vertex + 16 B per frontier entry per phase
+    alg_bytes = (16 * edges + 16 * settled + 16 * sum_f) / args.steps
+    achieved = alg_bytes / (kernel_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": None, "peak_kind": peak_kind, "kernel": "k_solve_grid" if not batched else "k_solve_batch"}
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if not batched:
+        gi, s = wl.solves[0]
+        g = wl.graphs[gi]
+        pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
+        ro, col, w = pin(g.row_off), pin(g.col), pin(g.w)
+        dist_h = torch.empty(g.n, dtype=torch.int64).pin_memory().numpy().view(np.uint64)
+        e2e_t, e2e_edges = 0.0, 0
+        reps = max(1, min(args.steps, 5))
+        for r in range(reps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            Gh = sp.Graph(g.n, ro, col, w, reverse=(args.criterion != "in_out"))
+            _, ph = sp.solve(Gh, s, crit, out=dist_h)
+            Gh.close()
+            dt = time.perf_counter() - t0
+            if r > 0:
+                e2e_t += dt
+                e2e_edges += per_solve[0]["edges_relaxed"]
+        e2e = {"value": ws * e2e_edges / e2e_t / 1e9, "unit": "GTEPS",
+               "h2d_bytes_per_step": int(ro.nbytes + col.nbytes + w.nbytes),
+               "d2h_bytes_per_step": int(dist_h.nbytes + 8), "includes": "graph create (H2D + preprocessing) + solve + D2H"}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(wl)
+    clocks = clk.summary()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": wl.name, "criterion": args.criterion, "solves_per_step": nsolves // args.steps,
+                       "phases_per_solve": phases / nsolves, "queries_per_s": ws * nsolves / (total_ms * 1e-3),
+                       "us_per_phase": 1e3 * total_ms / phases, "sum_frontier_per_solve": sum_f / nsolves,
+                       "prep_ms": prep_ms, "l2": "flushed between steps (2x L2 buffer written)",
+                       "parallelism": f"replicas x{ws}"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": args.steps, "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,210 @@
+/*
+ * sssp.h -- C ABI of the GB300 phase-parallel Dijkstra library.
+ *
+ * The library computes single-source shortest paths on a directed graph with
+ * non-negative integer edge costs (Section 2 of Kainer & Traeff, "More
+ * Parallelism in Dijkstra's Single-Source Shortest Path Algorithm",
+ * arXiv:1903.12085) with the generic phased algorithm of Section 3: in every
+ * phase, every fringe vertex that a correctness criterion proves final is
+ * settled at once, and all of their out-edges are relaxed together.
+ *
+ * Conventions shared by every entry point
+ *   - Vertices are 0..n-1.  Edge costs are uint32 and must be < 0xFFFFFFFF
+ *     (that value is the "no edge" sentinel of the minima).  Distances are
+ *     uint64; an unreachable vertex gets UINT64_MAX.  Limits: 1 <= n < 2^31,
+ *     m < 2^32.  Self-loops and parallel edges are accepted; they take part
+ *     in every minimum and never change a distance.
+ *   - All arithmetic is exact unsigned integer: results do not depend on the
+ *     order of relaxations, so distances and phase counts are unique.
+ *   - Every call returns an sssp_status.  Nothing is thrown across the ABI.
+ *     On failure, sssp_last_error() gives a message (thread-local).
+ *   - "stream" is a cudaStream_t passed as void*; NULL means the legacy
+ *     default stream.  Unless stated otherwise a call returns after the work
+ *     it queued on the stream has finished.
+ *   - The library allocates device memory only inside sssp_graph_create,
+ *     the first solve on a graph (its workspace) and sssp_batch_create; it
+ *     frees it in the matching destroy call.
+ *   - Solves on one graph handle share its workspace: do not run two solves
+ *     on the same handle at the same time (use sssp_solve_batch instead).
+ */
+#ifndef SSSP_GB300_H
+#define SSSP_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SSSP_OK = 0,
+  SSSP_ERR_INVALID_ARG = 1,   /* bad CSR, source >= n, reserved cost, bad mask */
+  SSSP_ERR_OUT_OF_MEMORY = 2, /* a device or host allocation failed */
+  SSSP_ERR_CUDA = 3,          /* a CUDA runtime call failed */
+  SSSP_ERR_TIMEOUT = 4,       /* an in-kernel wait exceeded its time limit */
+  SSSP_ERR_INTERNAL = 5,      /* a device-side consistency check failed */
+  SSSP_ERR_UNSUPPORTED = 6    /* option not available (e.g. IN-SIMPLE without reverse CSR) */
+} sssp_status;
+
+/* Criterion mask: a phase settles every fringe vertex v satisfying ANY of
+ * the criteria whose bits are set (a disjunction of sound criteria is sound,
+ * and complete if one disjunct is, Section 3).  With
+ * minD = min_{u in F} d[u] taken on the phase-start state:
+ *   SSSP_IN_STATIC   d[v] <= minD + min_{(w,v) in E} c(w,v)             (eq. crit:instatic)
+ *   SSSP_OUT_STATIC  d[v] <= min_{u in F} (d[u] + min_{(u,w) in E} c(u,w)) (eq. crit:outstatic)
+ *   SSSP_IN_SIMPLE   as IN_STATIC, minimum over in-edges from unsettled w  (eq. crit:insimple)
+ *   SSSP_OUT_SIMPLE  as OUT_STATIC, minimum over out-edges to unsettled w  (eq. crit:outsimple)
+ *   SSSP_DIJK        the single fringe vertex of minimum d, lowest id on ties (Section 3)
+ * An empty minimum is infinite: the IN test then holds, and the vertex adds
+ * nothing to the OUT threshold.  IN_SIMPLE needs a graph built with
+ * SSSP_GRAPH_REVERSE.  "IN+OUT" = SSSP_IN_STATIC | SSSP_OUT_STATIC is the
+ * criterion of the paper's implementation (Section 5). */
+enum {
+  SSSP_IN_STATIC = 1u << 0,
+  SSSP_OUT_STATIC = 1u << 1,
+  SSSP_IN_SIMPLE = 1u << 2,
+  SSSP_OUT_SIMPLE = 1u << 3,
+  SSSP_DIJK = 1u << 6,
+  SSSP_CRITERIA_MASK = 0xFFFFu,
+  /* Execution options (do not change results, only speed). */
+  SSSP_POLICY_LEARNED = 1u << 16,  /* per-phase arm chosen by the loaded policy network */
+  SSSP_FRONTIER_DENSE = 1u << 17,  /* scan the vertex-status array instead of the queue */
+  SSSP_FRONTIER_AUTO = 1u << 18    /* dense when |F| > n/8, else sparse */
+};
+
+/* sssp_graph_create build flags. */
+enum { SSSP_GRAPH_REVERSE = 1u << 0 /* also build the in-edge CSR */ };
+
+typedef struct sssp_graph sssp_graph;
+
+/*
+ * sssp_graph_create -- copy a CSR graph to the device and preprocess it.
+ *   row_offsets  uint64[n+1], non-decreasing, row_offsets[0] = 0,
+ *                row_offsets[n] = m; out-edges of u are [row_offsets[u],
+ *                row_offsets[u+1]) (the adjacency array of Section 5)
+ *   col_idx      uint32[m] edge targets, each < n
+ *   weights      uint32[m] edge costs, each < 0xFFFFFFFF
+ *   inputs_on_device  0: the three arrays are host memory; 1: device memory
+ *                (read during the call only)
+ * Preprocessing (Section 5 "Preprocessing" and Proposition 3): every out-row
+ * is sorted by (cost, target); the static out-minimum of u is the cost of
+ * its first edge; the static in-minimum of v is an atomic minimum over all
+ * edges into v; with SSSP_GRAPH_REVERSE the in-edge CSR is built and its
+ * rows sorted by (cost, source).  The caller keeps ownership of its arrays;
+ * the handle owns its device copies.  Invalid input -> SSSP_ERR_INVALID_ARG
+ * with nothing allocated (host inputs are checked on the host, device inputs
+ * by a device pass).  *out is set only on success.
+ */
+sssp_status sssp_graph_create(uint32_t n, uint64_t m, const uint64_t* row_offsets,
+                              const uint32_t* col_idx, const uint32_t* weights,
+                              int inputs_on_device, uint32_t build_flags, void* stream,
+                              sssp_graph** out);
+
+/* Frees the handle and every device buffer it owns.  NULL is ignored. */
+void sssp_graph_destroy(sssp_graph* g);
+
+/* n, m and build flags of a handle (any pointer may be NULL). */
+sssp_status sssp_graph_info(const sssp_graph* g, uint32_t* n, uint64_t* m, uint32_t* flags);
+
+/* Device copies held by a handle, for callers that inspect the preprocessed
+ * graph (any pointer may be NULL).  edges: uint32 pairs {target, cost} per
+ * edge, rows sorted by (cost, target); out_min/in_min: uint32[n] static
+ * minima (0xFFFFFFFF = no edge); rrow_off/redges: the in-edge CSR ({source,
+ * cost} pairs) or NULL.  The pointers stay valid until sssp_graph_destroy. */
+sssp_status sssp_graph_device_arrays(const sssp_graph* g, const uint64_t** row_off,
+                                     const uint32_t** edges, const uint32_t** out_min,
+                                     const uint32_t** in_min, const uint64_t** rrow_off,
+                                     const uint32_t** redges);
+
+/* Per-solve counters. */
+typedef struct {
+  uint64_t phases;         /* phases until F was empty (phase 1 settles the source) */
+  uint64_t sum_frontier;   /* sum over phases of |F| at the start of the phase */
+  uint64_t settled;        /* vertices settled (= vertices reachable from the source) */
+  uint64_t edges_relaxed;  /* sum of out-degrees of settled vertices (each edge once) */
+} sssp_stats;
+
+/* One record per phase (sssp_solve_trace).  64 bytes, little-endian. */
+typedef struct {
+  uint32_t frontier;       /* |F| at phase start */
+  uint32_t settled;        /* |S'| */
+  uint64_t min_d;          /* minD */
+  uint64_t min_out;        /* OUT threshold used (UINT64_MAX if none) */
+  uint64_t deg_settled;    /* sum of out-degrees of S' */
+  uint32_t criterion;      /* criterion mask applied in this phase */
+  uint32_t arm;            /* bit 0: dense frontier; bits 8..15: policy arm index */
+  uint64_t t_start_ns;     /* device %globaltimer at phase start */
+  uint64_t t_end_ns;       /* device %globaltimer at phase end */
+  uint64_t reserved;
+} sssp_phase_record;
+
+/*
+ * sssp_solve -- one shortest-path solve from `source` (Sections 2-3).
+ *   criterion   criterion mask plus execution options (see above); at least
+ *               one criterion bit.
+ *   dist_out    uint64[n], host or device memory (detected), caller-owned.
+ *               Receives dist(source, v), UINT64_MAX if unreachable.
+ *   phases_out  host uint64 (may be NULL): number of phases.
+ * Synchronous.  The first call on a handle allocates its workspace.
+ */
+sssp_status sssp_solve(sssp_graph* g, uint32_t source, uint32_t criterion, uint64_t* dist_out,
+                       uint64_t* phases_out, void* stream);
+
+/*
+ * sssp_solve_trace -- sssp_solve plus diagnostics (each output may be NULL):
+ *   stats         host sssp_stats
+ *   settle_phase  uint32[n], host or device: phase in which each vertex was
+ *                 settled (0 = never) -- the per-phase settled sets S'
+ *   trace         host array of trace_cap records; phases beyond trace_cap
+ *                 are not recorded
+ */
+sssp_status sssp_solve_trace(sssp_graph* g, uint32_t source, uint32_t criterion,
+                             uint64_t* dist_out, sssp_stats* stats, uint32_t* settle_phase,
+                             sssp_phase_record* trace, uint64_t trace_cap, void* stream);
+
+/*
+ * sssp_solve_batch -- `count` independent solves in one persistent launch:
+ * solve i runs on graphs[i] from sources[i] (graphs may repeat).  Blocks of
+ * the launch pull solves from a device work queue, largest graph first.
+ *   dist_out[i]  uint64[n_i] device memory
+ *   phases_out   uint64[count], host or device (detected); may be NULL
+ * Synchronous.  Workspaces are allocated per call; for repeated batches use
+ * sssp_batch_create / sssp_batch_launch.
+ */
+sssp_status sssp_solve_batch(sssp_graph* const* graphs, const uint32_t* sources, uint32_t count,
+                             uint32_t criterion, uint64_t* const* dist_out, uint64_t* phases_out,
+                             void* stream);
+
+/* A prepared batch: descriptors and workspaces allocated once, the launch
+ * captured in a CUDA graph.  sssp_batch_launch replays it on `stream`
+ * (stream-ordered, returns immediately); outputs are the device buffers given
+ * at creation.  phases_out must be device memory here. */
+typedef struct sssp_batch sssp_batch;
+sssp_status sssp_batch_create(sssp_graph* const* graphs, const uint32_t* sources, uint32_t count,
+                              uint32_t criterion, uint64_t* const* dist_out, uint64_t* phases_out,
+                              void* stream, sssp_batch** out);
+sssp_status sssp_batch_launch(sssp_batch* b, void* stream);
+void sssp_batch_destroy(sssp_batch* b);
+
+/* Upper bound, in nanoseconds, on any single in-kernel wait (grid barrier,
+ * work queue).  A wait that runs out sets SSSP_ERR_TIMEOUT and the kernel
+ * returns.  Default 2e9.  Applies to launches made after the call. */
+sssp_status sssp_set_wait_limit_ns(uint64_t ns);
+
+/* Self-test of the bounded in-kernel wait that every grid barrier uses: one
+ * thread waits on a device word that nothing writes, so the wait must run out
+ * after limit_ns.  Returns SSSP_ERR_TIMEOUT (the expected outcome) and leaves
+ * the CUDA context usable.  Allocates and frees two words of device memory. */
+sssp_status sssp_selftest_wait(uint64_t limit_ns);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* sssp_last_error(void);
+
+/* Library version string. */
+const char* sssp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SSSP_GB300_H */

@@ -1,0 +1,273 @@
+"""Python binding of the GB300 phase-parallel Dijkstra library (libsssp_gb300.so).
+
+Argument marshalling only: every step of a solve runs in the library's CUDA
+kernels behind the C ABI of ``include/sssp.h``.  PyTorch provides device
+memory and streams.  There is no CPU fallback: if the shared library is not
+built, every call raises.
+
+Names follow the C ABI::
+
+    g = Graph(n, row_off, col, w, reverse=True)      # sssp_graph_create
+    dist, phases = solve(g, source, IN_STATIC | OUT_STATIC)   # sssp_solve
+    dist, stats, settle, trace = solve_trace(g, source, crit)  # sssp_solve_trace
+    phases = solve_batch([g, ...], [s, ...], crit, outs)       # sssp_solve_batch
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsssp_gb300.so")
+
+# criterion mask bits and options (include/sssp.h)
+IN_STATIC = 1 << 0
+OUT_STATIC = 1 << 1
+IN_SIMPLE = 1 << 2
+OUT_SIMPLE = 1 << 3
+DIJK = 1 << 6
+POLICY_LEARNED = 1 << 16
+FRONTIER_DENSE = 1 << 17
+FRONTIER_AUTO = 1 << 18
+GRAPH_REVERSE = 1 << 0
+IN_OUT = IN_STATIC | OUT_STATIC
+SIMPLE = IN_SIMPLE | OUT_SIMPLE
+
+STATUS = {0: "SSSP_OK", 1: "SSSP_ERR_INVALID_ARG", 2: "SSSP_ERR_OUT_OF_MEMORY", 3: "SSSP_ERR_CUDA",
+          4: "SSSP_ERR_TIMEOUT", 5: "SSSP_ERR_INTERNAL", 6: "SSSP_ERR_UNSUPPORTED"}
+
+PHASE_RECORD = np.dtype([("frontier", "<u4"), ("settled", "<u4"), ("min_d", "<u8"), ("min_out", "<u8"),
+                         ("deg_settled", "<u8"), ("criterion", "<u4"), ("arm", "<u4"),
+                         ("t_start_ns", "<u8"), ("t_end_ns", "<u8"), ("reserved", "<u8")])
+assert PHASE_RECORD.itemsize == 64
+
+
+class SsspError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("phases", ctypes.c_uint64), ("sum_frontier", ctypes.c_uint64),
+                ("settled", ctypes.c_uint64), ("edges_relaxed", ctypes.c_uint64)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded shared library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                               "(there is no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        u32, u64, p, i32 = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_int
+        sig = {
+            "sssp_graph_create": [u32, u64, p, p, p, i32, u32, p, ctypes.POINTER(p)],
+            "sssp_graph_info": [p, p, p, p],
+            "sssp_graph_device_arrays": [p, p, p, p, p, p, p],
+            "sssp_solve": [p, u32, u32, p, p, p],
+            "sssp_solve_trace": [p, u32, u32, p, p, p, p, u64, p],
+            "sssp_solve_batch": [p, p, u32, u32, p, p, p],
+            "sssp_batch_create": [p, p, u32, u32, p, p, p, ctypes.POINTER(p)],
+            "sssp_batch_launch": [p, p],
+            "sssp_set_wait_limit_ns": [u64],
+            "sssp_selftest_wait": [u64],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = ctypes.c_int
+        L.sssp_graph_destroy.argtypes = [p]
+        L.sssp_graph_destroy.restype = None
+        L.sssp_batch_destroy.argtypes = [p]
+        L.sssp_batch_destroy.restype = None
+        L.sssp_last_error.restype = ctypes.c_char_p
+        L.sssp_version.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != 0:
+        raise SsspError(status, lib().sssp_last_error().decode())
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(x):
+    """Data pointer of a numpy array or torch tensor."""
+    if isinstance(x, np.ndarray):
+        return ctypes.c_void_p(x.ctypes.data)
+    return ctypes.c_void_p(x.data_ptr())
+
+
+def version() -> str:
+    return lib().sssp_version().decode()
+
+
+def set_wait_limit_ns(ns: int):
+    _check(lib().sssp_set_wait_limit_ns(int(ns)))
+
+
+def selftest_wait(limit_ns: int) -> int:
+    """sssp_selftest_wait: status of a bounded wait on a word nothing writes
+    (SSSP_ERR_TIMEOUT = 4 is the expected result)."""
+    return int(lib().sssp_selftest_wait(int(limit_ns)))
+
+
+class Graph:
+    """A preprocessed graph on the current CUDA device (sssp_graph_create).
+
+    ``row_off``/``col``/``w`` are either numpy arrays (host) or CUDA tensors
+    (device; uint64/int64 offsets, uint32/int32 targets and costs)."""
+
+    def __init__(self, n: int, row_off, col, w, reverse: bool = False, stream=None):
+        on_dev = not isinstance(row_off, np.ndarray)
+        if not on_dev:
+            row_off = np.ascontiguousarray(row_off, dtype=np.uint64)
+            col = np.ascontiguousarray(col, dtype=np.uint32)
+            w = np.ascontiguousarray(w, dtype=np.uint32)
+            m = int(col.shape[0])
+        else:
+            m = int(col.numel())
+        self.n, self.m = int(n), m
+        self._keep = (row_off, col, w)
+        h = ctypes.c_void_p()
+        _check(lib().sssp_graph_create(self.n, m, _ptr(row_off), _ptr(col), _ptr(w), int(on_dev),
+                                       GRAPH_REVERSE if reverse else 0, _stream_ptr(stream), ctypes.byref(h)))
+        self._keep = None
+        self.handle = h
+        self.reverse = reverse
+
+    @classmethod
+    def from_csr(cls, g, reverse: bool = False, stream=None) -> "Graph":
+        """From any object with n, row_off, col, w (e.g. graphgen.Graph)."""
+        return cls(g.n, g.row_off, g.col, g.w, reverse=reverse, stream=stream)
+
+    def device_arrays(self):
+        """Preprocessed device arrays as torch tensors (views, no copy)."""
+        torch = _torch()
+        ptrs = [ctypes.c_void_p() for _ in range(6)]
+        _check(lib().sssp_graph_device_arrays(self.handle, *[ctypes.byref(x) for x in ptrs]))
+        return {name: p.value for name, p in zip(["row_off", "edges", "out_min", "in_min", "rrow_off", "redges"], ptrs)}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().sssp_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _dist_buffer(n, out):
+    torch = _torch()
+    if out is None:
+        out = torch.empty(n, dtype=torch.int64, device="cuda")
+    return out
+
+
+def solve(g: Graph, source: int, criterion: int = IN_OUT, out=None, stream=None):
+    """sssp_solve.  Returns (dist, phases); dist is ``out`` if given (a CUDA
+    int64/uint64 tensor or a numpy uint64 array), else a new CUDA int64 tensor
+    holding the uint64 bit patterns (view with ``as_uint64``)."""
+    out = _dist_buffer(g.n, out)
+    phases = ctypes.c_uint64()
+    _check(lib().sssp_solve(g.handle, int(source), int(criterion), _ptr(out), ctypes.byref(phases),
+                            _stream_ptr(stream)))
+    return out, phases.value
+
+
+def solve_trace(g: Graph, source: int, criterion: int = IN_OUT, out=None, trace_cap: int = 0,
+                settle: bool = True, stream=None):
+    """sssp_solve_trace.  Returns (dist, stats dict, settle_phase numpy uint32
+    or None, trace numpy records or None)."""
+    out = _dist_buffer(g.n, out)
+    st = _Stats()
+    sp = np.zeros(g.n, np.uint32) if settle else None
+    tr = np.zeros(trace_cap, PHASE_RECORD) if trace_cap else None
+    _check(lib().sssp_solve_trace(g.handle, int(source), int(criterion), _ptr(out), ctypes.byref(st),
+                                  _ptr(sp) if sp is not None else None,
+                                  _ptr(tr) if tr is not None else None, int(trace_cap), _stream_ptr(stream)))
+    stats = {"phases": st.phases, "sum_frontier": st.sum_frontier, "settled": st.settled,
+             "edges_relaxed": st.edges_relaxed}
+    if tr is not None:
+        tr = tr[:min(trace_cap, st.phases)]
+    return out, stats, sp, tr
+
+
+def _ptr_array(objs):
+    arr = (ctypes.c_void_p * len(objs))()
+    for i, o in enumerate(objs):
+        arr[i] = o.handle.value if isinstance(o, Graph) else _ptr(o).value
+    return arr
+
+
+def solve_batch(graphs, sources, criterion: int = IN_OUT, outs=None, stream=None):
+    """sssp_solve_batch.  ``outs``: list of CUDA tensors (n_i each), allocated
+    if None.  Returns (outs, phases numpy uint64)."""
+    torch = _torch()
+    if outs is None:
+        outs = [torch.empty(g.n, dtype=torch.int64, device="cuda") for g in graphs]
+    src = np.ascontiguousarray(sources, dtype=np.uint32)
+    phases = np.zeros(len(graphs), np.uint64)
+    _check(lib().sssp_solve_batch(_ptr_array(graphs), _ptr(src), len(graphs), int(criterion), _ptr_array(outs),
+                                  _ptr(phases), _stream_ptr(stream)))
+    return outs, phases
+
+
+class Batch:
+    """A prepared batch (sssp_batch_create): descriptors, workspaces and the
+    launch captured once in a CUDA graph; ``launch()`` replays it."""
+
+    def __init__(self, graphs, sources, criterion: int = IN_OUT, outs=None, stream=None):
+        torch = _torch()
+        self.graphs = list(graphs)
+        self.outs = outs if outs is not None else [torch.empty(g.n, dtype=torch.int64, device="cuda")
+                                                   for g in self.graphs]
+        self.phases = torch.zeros(len(self.graphs), dtype=torch.int64, device="cuda")
+        src = np.ascontiguousarray(sources, dtype=np.uint32)
+        h = ctypes.c_void_p()
+        _check(lib().sssp_batch_create(_ptr_array(self.graphs), _ptr(src), len(self.graphs), int(criterion),
+                                       _ptr_array(self.outs), _ptr(self.phases), _stream_ptr(stream),
+                                       ctypes.byref(h)))
+        self.handle = h
+
+    def launch(self, stream=None):
+        _check(lib().sssp_batch_launch(self.handle, _stream_ptr(stream)))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().sssp_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def as_uint64(x) -> np.ndarray:
+    """uint64 numpy view of a distance buffer (CUDA tensor or numpy array)."""
+    if isinstance(x, np.ndarray):
+        return x.view(np.uint64)
+    return x.detach().cpu().numpy().view(np.uint64)

@@ -1,0 +1,82 @@
+// capi.cu -- error reporting and small utilities behind the C ABI.
+#include <atomic>
+#include <cstdio>
+
+#include "internal.h"
+
+namespace sssp {
+
+namespace {
+thread_local char t_err[512] = "";
+std::atomic<uint64_t> g_wait_ns{2000000000ull};
+}  // namespace
+
+sssp_status fail(sssp_status st, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(t_err, sizeof t_err, fmt, ap);
+  va_end(ap);
+  return st;
+}
+
+void clear_error() { t_err[0] = '\0'; }
+
+uint64_t wait_limit_ns() { return g_wait_ns.load(); }
+
+bool is_device_pointer(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int sm_count() {
+  static int cached = 0;
+  if (!cached) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&cached, cudaDevAttrMultiProcessorCount, dev);
+    if (cached <= 0) cached = 1;
+  }
+  return cached;
+}
+
+}  // namespace sssp
+
+namespace sssp {
+namespace {
+// Waits on a word that nothing writes: the wait must run out.
+__global__ void k_selftest_wait(const unsigned int* flag, unsigned long long limit_ns, int* err) {
+  if (threadIdx.x == 0) bounded_wait_change(flag, 0u, limit_ns, err);
+}
+}  // namespace
+}  // namespace sssp
+
+extern "C" sssp_status sssp_selftest_wait(uint64_t limit_ns) {
+  sssp::clear_error();
+  unsigned int* flag = nullptr;
+  int* err = nullptr;
+  int herr = 0;
+  SSSP_CUDA_TRY(cudaMalloc(&flag, sizeof(unsigned int)));
+  SSSP_CUDA_TRY(cudaMalloc(&err, sizeof(int)));
+  SSSP_CUDA_TRY(cudaMemset(flag, 0, sizeof(unsigned int)));
+  SSSP_CUDA_TRY(cudaMemset(err, 0, sizeof(int)));
+  sssp::k_selftest_wait<<<1, 32>>>(flag, limit_ns, err);
+  SSSP_CUDA_TRY(cudaGetLastError());
+  SSSP_CUDA_TRY(cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost));
+  cudaFree(flag);
+  cudaFree(err);
+  if (herr != 0) return sssp::fail((sssp_status)herr, "bounded wait gave up as designed");
+  return SSSP_OK;
+}
+
+extern "C" sssp_status sssp_set_wait_limit_ns(uint64_t ns) {
+  sssp::g_wait_ns.store(ns);
+  return SSSP_OK;
+}
+
+extern "C" const char* sssp_last_error(void) { return sssp::t_err; }
+
+extern "C" const char* sssp_version(void) { return "sssp-gb300 0.1 (sm_103a)"; }

@@ -1,0 +1,79 @@
+// internal.h -- host-side helpers shared by the library's translation units.
+#pragma once
+
+#include <cstdarg>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/sssp.h"
+#include "common.cuh"
+
+namespace sssp {
+
+// Records a message for sssp_last_error() and returns `st`.
+sssp_status fail(sssp_status st, const char* fmt, ...);
+void clear_error();
+
+// Wait limit of in-kernel waits (ns).
+uint64_t wait_limit_ns();
+
+// Returns true if p points to device (or managed) memory.
+bool is_device_pointer(const void* p);
+
+// Number of SMs of the current device.
+int sm_count();
+
+}  // namespace sssp
+
+#define SSSP_CUDA_TRY(expr)                                                                  \
+  do {                                                                                       \
+    cudaError_t e_ = (expr);                                                                 \
+    if (e_ != cudaSuccess) {                                                                 \
+      return ::sssp::fail(e_ == cudaErrorMemoryAllocation ? SSSP_ERR_OUT_OF_MEMORY           \
+                                                          : SSSP_ERR_CUDA,                   \
+                          "%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, \
+                          __LINE__);                                                         \
+    }                                                                                        \
+  } while (0)
+
+namespace sssp {
+struct Workspace;
+}
+
+// Host-visible graph handle.
+struct sssp_graph {
+  uint32_t n;
+  uint64_t m;
+  uint32_t flags;
+  int device;
+  uint64_t* row_off;   // device [n+1]
+  uint2* edges;        // device [m]
+  uint32_t* out_min;   // device [n]
+  uint32_t* in_min;    // device [n]
+  uint64_t* rrow_off;  // device [n+1] or nullptr
+  uint2* redges;       // device [m] or nullptr
+  // Lazily allocated solve workspace (shared by solves on this handle).
+  sssp::Workspace* ws;
+};
+
+namespace sssp {
+
+struct Workspace {
+  uint32_t n;
+  unsigned long long* d;
+  uint8_t* status;
+  uint32_t* q0;
+  uint32_t* q1;
+  uint32_t* sp_v;
+  uint32_t* sp_base;
+  uint32_t* cur_out;
+  uint32_t* cur_in;
+  Ctl* ctl;
+  Ctl* ctl_host;  // pinned mirror for read-back
+};
+
+GraphView view_of(const sssp_graph* g);
+sssp_status workspace_get(sssp_graph* g, Workspace** out);
+void workspace_free(Workspace* ws);
+
+}  // namespace sssp

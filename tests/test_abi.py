@@ -1,0 +1,52 @@
+"""The C-ABI library loads and exports every function include/*.h declares
+(no GPU needed: only symbols are looked up, nothing is called)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(sssp_\w+)\s*\(", text):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ["sssp_graph_create", "sssp_graph_destroy", "sssp_solve", "sssp_solve_batch",
+                     "sssp_solve_trace", "sssp_last_error"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_function():
+    import paper_1903_12085_gb300 as sp
+    if not os.path.exists(sp.LIB_PATH):
+        from paper_1903_12085_gb300 import _build
+        _build.build()
+    lib = ctypes.CDLL(sp.LIB_PATH)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_version_string_without_gpu():
+    import paper_1903_12085_gb300 as sp
+    assert "sm_103a" in sp.version()
+
+
+def test_product_path_does_not_touch_oracle():
+    """The package never imports, links or loads the oracle (no CPU fallback)."""
+    pkg = os.path.join(ROOT, "paper_1903_12085_gb300")
+    for path in glob.glob(os.path.join(pkg, "**", "*"), recursive=True):
+        if os.path.isfile(path) and path.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+            text = open(path).read()
+            for bad in ("import oracle", "from oracle", "liboracle", "oracle.c"):
+                assert bad not in text, (path, bad)
