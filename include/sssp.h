@@ -187,6 +187,37 @@ sssp_status sssp_batch_create(sssp_graph* const* graphs, const uint32_t* sources
 sssp_status sssp_batch_launch(sssp_batch* b, void* stream);
 void sssp_batch_destroy(sssp_batch* b);
 
+/* Largest n accepted by sssp_solve_noalloc. */
+#define SSSP_NOALLOC_MAX_VERTICES (1u << 20)
+
+/*
+ * sssp_solve_noalloc -- a solve that allocates nothing (the paper has no
+ * counterpart; it exists for callers that cannot allocate device memory at
+ * solve time, e.g. an application whose allocator has reserved the whole
+ * device up front, or a latency-critical service that cannot take the
+ * implicit device synchronisation of cudaMalloc/cudaFree in its request path).
+ *   row_offsets  uint64[n+1] device memory (as in sssp_graph_create)
+ *   edges        uint32 pairs {target, cost}, 2*m words, device memory; rows
+ *                need not be sorted
+ *   criterion    SSSP_IN_STATIC, SSSP_OUT_STATIC and/or SSSP_DIJK (plus the
+ *                frontier options); other criteria -> SSSP_ERR_UNSUPPORTED
+ *   dist_out     uint64[n] device memory, receives the distances
+ *   phases_out   host uint64 (may be NULL)
+ * n must be in [1, SSSP_NOALLOC_MAX_VERTICES]; larger graphs are rejected with
+ * SSSP_ERR_INVALID_ARG.  All scratch (status, queues, relax list, static
+ * minima, control block: about 25 bytes per vertex of the maximum, 25 MiB in
+ * all) is one file-scope __device__ array that every GPU loading the library
+ * holds until the process exits.  The call makes no cudaMalloc/cudaFree or
+ * other allocating call.  Its first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) and the co-resident block count; make
+ * that first call before any stream capture.  Every call reuses the same
+ * array: it clears the control block itself, and calls that overlap on the
+ * GPU (two streams, two host threads) race on the array.  Synchronous.
+ */
+sssp_status sssp_solve_noalloc(uint32_t n, uint64_t m, const uint64_t* row_offsets,
+                               const uint32_t* edges, uint32_t source, uint32_t criterion,
+                               uint64_t* dist_out, uint64_t* phases_out, void* stream);
+
 /* Upper bound, in nanoseconds, on any single in-kernel wait (grid barrier,
  * work queue).  A wait that runs out sets SSSP_ERR_TIMEOUT and the kernel
  * returns.  Default 2e9.  Applies to launches made after the call. */

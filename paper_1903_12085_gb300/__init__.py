@@ -78,6 +78,7 @@ def lib():
             "sssp_batch_launch": [p, p],
             "sssp_set_wait_limit_ns": [u64],
             "sssp_selftest_wait": [u64],
+            "sssp_solve_noalloc": [u32, u64, p, p, u32, u32, p, p, p],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -212,6 +213,23 @@ def solve_trace(g: Graph, source: int, criterion: int = IN_OUT, out=None, trace_
     if tr is not None:
         tr = tr[:min(trace_cap, st.phases)]
     return out, stats, sp, tr
+
+
+NOALLOC_MAX_VERTICES = 1 << 20
+
+
+def solve_noalloc(n: int, row_off, edges, source: int, criterion: int = IN_OUT, out=None, stream=None):
+    """sssp_solve_noalloc: a solve that allocates no device memory.  ``row_off``
+    (int64/uint64, n+1) and ``edges`` (int32/uint32 pairs {target, cost}, 2*m)
+    are CUDA tensors; ``out`` a CUDA int64 tensor of n (allocated here by torch
+    if None -- pass it in to keep the whole call allocation-free).  Returns
+    (dist, phases)."""
+    out = _dist_buffer(n, out)
+    phases = ctypes.c_uint64()
+    m = int(edges.numel()) // 2
+    _check(lib().sssp_solve_noalloc(int(n), m, _ptr(row_off), _ptr(edges), int(source), int(criterion), _ptr(out),
+                                    ctypes.byref(phases), _stream_ptr(stream)))
+    return out, phases.value
 
 
 def _ptr_array(objs):

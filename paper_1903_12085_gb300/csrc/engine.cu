@@ -34,24 +34,10 @@
 #include <cstring>
 #include <vector>
 
+#include "engine.h"
 #include "internal.h"
 
 namespace sssp {
-
-constexpr int kThreads = 512;
-constexpr int kRelaxItems = 4;
-constexpr int kTile = kThreads * kRelaxItems;
-constexpr size_t kSmemBytes = 64 * sizeof(unsigned long long)                  // reduction scratch
-                              + kTile * (sizeof(uint32_t) + 2 * sizeof(unsigned long long))  // relax tile
-                              + 16;
-
-struct SolveParams {
-  GraphView g;
-  SolveWS ws;
-  uint32_t source;
-  uint32_t crit;
-  unsigned long long wait_ns;
-};
 
 struct GridGroup {
   GridBarrier* bar;
