@@ -188,7 +188,7 @@ sssp_status sssp_batch_launch(sssp_batch* b, void* stream);
 void sssp_batch_destroy(sssp_batch* b);
 
 /* Largest n accepted by sssp_solve_noalloc. */
-#define SSSP_NOALLOC_MAX_VERTICES (1u << 20)
+#define SSSP_NOALLOC_MAX_VERTICES (1u << 19)
 
 /*
  * sssp_solve_noalloc -- a solve that allocates nothing (the paper has no
@@ -204,9 +204,9 @@ void sssp_batch_destroy(sssp_batch* b);
  *   dist_out     uint64[n] device memory, receives the distances
  *   phases_out   host uint64 (may be NULL)
  * n must be in [1, SSSP_NOALLOC_MAX_VERTICES]; larger graphs are rejected with
- * SSSP_ERR_INVALID_ARG.  All scratch (status, queues, relax list, static
- * minima, control block: about 25 bytes per vertex of the maximum, 25 MiB in
- * all) is one file-scope __device__ array that every GPU loading the library
+ * SSSP_ERR_INVALID_ARG.  All scratch (status, queues, relax list, distance
+ * records, static minima, control block: 49 bytes per vertex of the maximum,
+ * about 25 MiB in all) is one file-scope __device__ array that every GPU loading the library
  * holds until the process exits.  The call makes no cudaMalloc/cudaFree or
  * other allocating call.  Its first call on a device looks up the array's
  * device address (cudaGetSymbolAddress) and the co-resident block count; make
@@ -217,6 +217,22 @@ void sssp_batch_destroy(sssp_batch* b);
 sssp_status sssp_solve_noalloc(uint32_t n, uint64_t m, const uint64_t* row_offsets,
                                const uint32_t* edges, uint32_t source, uint32_t criterion,
                                uint64_t* dist_out, uint64_t* phases_out, void* stream);
+
+/* Execution tuning (results never depend on it).  solo_max_frontier: phases
+ * whose fringe has at most this many vertices run on a single block with block
+ * barriers (0 = never); batch_blocks_per_solve: blocks that cooperate on one
+ * solve of a batch (0 = chosen from the batch); grid_blocks: blocks of a single
+ * solve (0 = chosen from n, capped at the co-resident maximum).  Applies to
+ * launches made after the call; sssp_set_tuning(NULL) restores the defaults
+ * (8192, 0, 0). */
+typedef struct {
+  uint32_t solo_max_frontier;
+  uint32_t batch_blocks_per_solve;
+  uint32_t grid_blocks;
+  uint32_t reserved[5];
+} sssp_tuning;
+sssp_status sssp_set_tuning(const sssp_tuning* t);
+sssp_status sssp_get_tuning(sssp_tuning* t);
 
 /* Upper bound, in nanoseconds, on any single in-kernel wait (grid barrier,
  * work queue).  A wait that runs out sets SSSP_ERR_TIMEOUT and the kernel

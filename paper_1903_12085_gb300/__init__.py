@@ -79,6 +79,8 @@ def lib():
             "sssp_set_wait_limit_ns": [u64],
             "sssp_selftest_wait": [u64],
             "sssp_solve_noalloc": [u32, u64, p, p, u32, u32, p, p, p],
+            "sssp_set_tuning": [p],
+            "sssp_get_tuning": [p],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -129,6 +131,33 @@ def selftest_wait(limit_ns: int) -> int:
     """sssp_selftest_wait: status of a bounded wait on a word nothing writes
     (SSSP_ERR_TIMEOUT = 4 is the expected result)."""
     return int(lib().sssp_selftest_wait(int(limit_ns)))
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("solo_max_frontier", ctypes.c_uint32), ("batch_blocks_per_solve", ctypes.c_uint32),
+                ("grid_blocks", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 5)]
+
+
+def set_tuning(solo_max_frontier=None, batch_blocks_per_solve=None, grid_blocks=None):
+    """sssp_set_tuning; unspecified fields keep their current value.
+    set_tuning() with no argument restores the defaults."""
+    if solo_max_frontier is None and batch_blocks_per_solve is None and grid_blocks is None:
+        _check(lib().sssp_set_tuning(None))
+        return
+    t = get_tuning()
+    if grid_blocks is not None:
+        t.grid_blocks = int(grid_blocks)
+    if solo_max_frontier is not None:
+        t.solo_max_frontier = int(solo_max_frontier)
+    if batch_blocks_per_solve is not None:
+        t.batch_blocks_per_solve = int(batch_blocks_per_solve)
+    _check(lib().sssp_set_tuning(ctypes.byref(t)))
+
+
+def get_tuning() -> Tuning:
+    t = Tuning()
+    _check(lib().sssp_get_tuning(ctypes.byref(t)))
+    return t
 
 
 class Graph:
@@ -215,7 +244,7 @@ def solve_trace(g: Graph, source: int, criterion: int = IN_OUT, out=None, trace_
     return out, stats, sp, tr
 
 
-NOALLOC_MAX_VERTICES = 1 << 20
+NOALLOC_MAX_VERTICES = 1 << 19
 
 
 def solve_noalloc(n: int, row_off, edges, source: int, criterion: int = IN_OUT, out=None, stream=None):

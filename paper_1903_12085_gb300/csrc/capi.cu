@@ -2,6 +2,7 @@
 #include <atomic>
 #include <cstdio>
 
+#include "engine.h"
 #include "internal.h"
 
 namespace sssp {
@@ -9,7 +10,14 @@ namespace sssp {
 namespace {
 thread_local char t_err[512] = "";
 std::atomic<uint64_t> g_wait_ns{2000000000ull};
+std::atomic<uint32_t> g_solo_max{kSoloMaxDefault};
+std::atomic<uint32_t> g_batch_bpg{0};
+std::atomic<uint32_t> g_grid_blocks{0};
 }  // namespace
+
+uint32_t solo_max() { return g_solo_max.load(); }
+uint32_t batch_blocks_per_solve() { return g_batch_bpg.load(); }
+uint32_t grid_blocks() { return g_grid_blocks.load(); }
 
 sssp_status fail(sssp_status st, const char* fmt, ...) {
   va_list ap;
@@ -69,6 +77,28 @@ extern "C" sssp_status sssp_selftest_wait(uint64_t limit_ns) {
   cudaFree(flag);
   cudaFree(err);
   if (herr != 0) return sssp::fail((sssp_status)herr, "bounded wait gave up as designed");
+  return SSSP_OK;
+}
+
+extern "C" sssp_status sssp_set_tuning(const sssp_tuning* t) {
+  if (!t) {
+    sssp::g_solo_max.store(sssp::kSoloMaxDefault);
+    sssp::g_batch_bpg.store(0);
+    sssp::g_grid_blocks.store(0);
+    return SSSP_OK;
+  }
+  sssp::g_solo_max.store(t->solo_max_frontier);
+  sssp::g_batch_bpg.store(t->batch_blocks_per_solve);
+  sssp::g_grid_blocks.store(t->grid_blocks);
+  return SSSP_OK;
+}
+
+extern "C" sssp_status sssp_get_tuning(sssp_tuning* t) {
+  if (!t) return sssp::fail(SSSP_ERR_INVALID_ARG, "tuning is NULL");
+  *t = sssp_tuning{};
+  t->solo_max_frontier = sssp::g_solo_max.load();
+  t->batch_blocks_per_solve = sssp::g_batch_bpg.load();
+  t->grid_blocks = sssp::g_grid_blocks.load();
   return SSSP_OK;
 }
 

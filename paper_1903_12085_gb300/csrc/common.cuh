@@ -1,8 +1,8 @@
 // common.cuh -- device primitives and shared structures of the phase engine.
 //
 // Everything here is plain integer work: 64-bit min-reductions (warp shuffle ->
-// block shared memory -> one global atomic), warp-aggregated queue appends, and a
-// grid barrier whose waits are bounded by %globaltimer so that a lost block can
+// block shared memory -> one global atomic), warp-aggregated queue appends, and
+// barriers whose waits are bounded by %globaltimer so that a lost block can
 // never hang the GPU (the wait gives up, records SSSP_ERR_TIMEOUT and returns).
 #pragma once
 
@@ -31,37 +31,68 @@ struct GraphView {
   const uint2* redges;       // [m] {source, cost}, rows sorted by (cost, source)
 };
 
-struct GridBarrier {
-  unsigned int count;
-  unsigned int gen;
+// Per-vertex record gathered by the selection step: the tentative distance and
+// the minima the criteria compare it with, in one 16-byte record so that a
+// fringe entry costs one sector.  d is updated with 64-bit atomicMin.
+//   im: in-minimum  (static, or the dynamic one when IN-SIMPLE maintains it)
+//   om: out-minimum (static, or the dynamic one when OUT-SIMPLE maintains it)
+struct __align__(16) VRec {
+  unsigned long long d;
+  uint32_t im;
+  uint32_t om;
 };
 
-// Per-solve control block in device memory.  Slots indexed [2] alternate by
-// phase parity so the next phase's slot can be reset while this one is read.
+// Relax-list entry of a settled vertex with out-edges: its distance, the start
+// of its out-row and the exclusive prefix of out-degrees over the list.
+struct __align__(16) SpEnt {
+  unsigned long long d;
+  uint32_t row;
+  uint32_t base;
+};
+
+// Bounded barrier over `size` blocks: one 32-bit counter.  Block 0 of the group
+// adds 2^31 - (size - 1), the others add 1, so the top bit flips exactly when
+// all have arrived (and the low bits return to their old value).
+struct GridBarrier {
+  unsigned int count;
+  unsigned int pad;
+};
+
+// Per-phase accumulators, triple-buffered: slot k % 3 belongs to phase k.
+// It is reset at the top of phase k - 2, filled during phase k - 1 (the
+// thresholds and queue of phase k) and phase k (relax list), and read in phase k.
+struct PhaseSlot {
+  unsigned long long min_d;       // fused thresholds of this phase (from phase k-1)
+  unsigned long long min_out;
+  unsigned long long a_min_d;     // thresholds recomputed by step A (three-step kind)
+  unsigned long long a_min_out;
+  unsigned long long relax_packed;  // (entries << 32) | edges of this phase's relax list
+  unsigned int qcount;            // |F| of this phase
+  unsigned int argmin;            // DIJK: lowest id of minimum d
+  unsigned int settled_now;       // |S'| of this phase
+  unsigned int pad;
+};
+
+// Per-solve control block in device memory (zeroed before each launch).
 struct Ctl {
-  unsigned long long min_d[2];
-  unsigned long long min_out[2];
-  unsigned int argmin[2];
-  unsigned int qcount[2];            // |F| of the queue with that parity
-  unsigned long long relax_packed;   // (entries << 32) | edges of this phase's relax list
-  unsigned int settled_now;          // |S'| of this phase (including degree-0 vertices)
-  unsigned int pad0;
+  PhaseSlot slot[3];
   unsigned long long phases, sum_f, settled, relaxed;
-  int err;                           // sssp_status set by a device-side failure
-  unsigned int done;
+  int err;                  // sssp_status recorded by a device-side failure
+  unsigned int gate;        // solo mode: bumped when the leader hands back to the group
+  unsigned long long heartbeat;  // solo mode: phases done by the leader (progress for waiters)
+  unsigned long long next_phase; // solo mode: phase the group resumes at (0 = solve finished)
   GridBarrier bar;
-  unsigned long long t_phase_start;
 };
 
 // Mutable per-solve buffers.
 struct SolveWS {
-  unsigned long long* d;   // [n] tentative distances
+  VRec* vrec;              // [n]
   uint8_t* status;         // [n]
-  uint32_t* q[2];          // [n] fringe queues (current / next)
-  uint32_t* sp_v;          // [n] relax list: settled vertices with out-degree > 0
-  uint32_t* sp_base;       // [n] exclusive prefix of their out-degrees
+  uint32_t* q[2];          // [n] fringe queues (this phase / next phase)
+  SpEnt* sp;               // [n] relax list
   uint32_t* cur_out;       // [n] out-row cursor (dynamic out-minimum), or nullptr
   uint32_t* cur_in;        // [n] in-row cursor (dynamic in-minimum), or nullptr
+  unsigned long long* dist;  // [n] output distances
   Ctl* ctl;
   uint32_t* settle_phase;  // [n] optional
   sssp_phase_record* trace;  // optional
@@ -83,6 +114,18 @@ __device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int* p) {
   return v;
 }
 
+__device__ __forceinline__ unsigned long long ld_relaxed_gpu_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned int atom_add_acq_rel_gpu(unsigned int* p, unsigned int v) {
+  unsigned int old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+
 __device__ __forceinline__ void red_release_gpu_add(unsigned int* p, unsigned int v) {
   asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
@@ -97,6 +140,22 @@ __device__ __forceinline__ uint32_t ldcg_u32(const uint32_t* p) { return __ldcg(
 __device__ __forceinline__ uint8_t ldcg_u8(const uint8_t* p) {
   return (uint8_t)__ldcg(reinterpret_cast<const unsigned char*>(p));
 }
+__device__ __forceinline__ VRec ldcg_vrec(const VRec* p) {
+  const ulonglong2 x = __ldcg(reinterpret_cast<const ulonglong2*>(p));
+  VRec r;
+  r.d = x.x;
+  r.im = (uint32_t)x.y;
+  r.om = (uint32_t)(x.y >> 32);
+  return r;
+}
+__device__ __forceinline__ SpEnt ldcg_sp(const SpEnt* p) {
+  const ulonglong2 x = __ldcg(reinterpret_cast<const ulonglong2*>(p));
+  SpEnt r;
+  r.d = x.x;
+  r.row = (uint32_t)x.y;
+  r.base = (uint32_t)(x.y >> 32);
+  return r;
+}
 
 // ---------------------------------------------------------------------------
 // Reductions and appends
@@ -110,10 +169,6 @@ __device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v)
   return v;
 }
 
-__device__ __forceinline__ uint32_t warp_sum_u32(uint32_t v) {
-  return __reduce_add_sync(0xFFFFFFFFu, v);
-}
-
 // Inclusive prefix sum within a full warp.
 __device__ __forceinline__ uint32_t warp_inclusive_scan(uint32_t v) {
   const int lane = threadIdx.x & 31;
@@ -125,8 +180,9 @@ __device__ __forceinline__ uint32_t warp_inclusive_scan(uint32_t v) {
   return v;
 }
 
-// Block-wide min of two u64 values, then one atomicMin per block into dst0/dst1.
-// Every thread of the block must call it.  scratch: 2 * 32 u64 of shared memory.
+// Block-wide min of two u64 values, then one atomicMin per block into dst0/dst1
+// (skipped for a null destination or an infinite value).  Every thread of the
+// block must call it.  scratch: 64 u64 of shared memory.
 __device__ __forceinline__ void block_min2_to_global(unsigned long long a, unsigned long long b,
                                                      unsigned long long* dst0, unsigned long long* dst1,
                                                      unsigned long long* scratch) {
@@ -168,17 +224,28 @@ __device__ __forceinline__ void warp_append(uint32_t* q, unsigned int* count, bo
 }
 
 // ---------------------------------------------------------------------------
-// Bounded wait: spin until *addr != old.  Gives up after limit_ns of
-// %globaltimer (recording SSSP_ERR_TIMEOUT in *err) or as soon as another
-// thread has recorded an error.  Returns true if the value changed.
+// Bounded waits
+
+// Spin until *addr != old.  Gives up after limit_ns of %globaltimer (recording
+// SSSP_ERR_TIMEOUT in *err) or as soon as an error has been recorded.  When
+// `progress` is given, the limit counts from the last change of *progress
+// (a heartbeat another block advances while it works).  Returns true if the
+// value changed.
 __device__ __forceinline__ bool bounded_wait_change(const unsigned int* addr, unsigned int old,
-                                                    unsigned long long limit_ns, int* err) {
-  const unsigned long long t0 = globaltimer_ns();
+                                                    unsigned long long limit_ns, int* err,
+                                                    const unsigned long long* progress = nullptr) {
+  unsigned long long t0 = globaltimer_ns();
+  unsigned long long last = progress ? ld_relaxed_gpu_u64(progress) : 0;
   unsigned int spins = 0;
   while (ld_acquire_gpu(addr) == old) {
     if ((++spins & 15u) == 0) {
       if (*(volatile int*)err != 0) return false;
-      if (globaltimer_ns() - t0 > limit_ns) {
+      const unsigned long long now = globaltimer_ns();
+      if (progress) {
+        const unsigned long long p = ld_relaxed_gpu_u64(progress);
+        if (p != last) { last = p; t0 = now; }
+      }
+      if (now - t0 > limit_ns) {
         atomicCAS(err, 0, (int)SSSP_ERR_TIMEOUT);
         return false;
       }
@@ -187,28 +254,33 @@ __device__ __forceinline__ bool bounded_wait_change(const unsigned int* addr, un
   return true;
 }
 
-// Grid barrier for cooperative (co-resident) launches: one arrival counter and
-// a generation word; the last block to arrive resets the counter and bumps the
-// generation, the others wait with bounded_wait_change.  Returns false (in
-// every thread of the block) if the wait ran out or any block recorded an
-// error, so that all blocks leave the solve.  All threads must call it.
-__device__ __forceinline__ bool grid_sync(GridBarrier* bar, unsigned int nblocks, unsigned long long limit_ns,
-                                          int* err) {
+// Barrier over the `size` blocks of a group (all co-resident).  rank 0 adds
+// 2^31 - (size - 1), the others 1; each block then waits (bounded) until the
+// counter's top bit differs from the one it saw.  The arrival is an acq_rel
+// atomic after a fence, so every write of the block before the barrier is
+// visible to every block after it.  Returns false in every thread of the block
+// if the wait ran out or an error was recorded.  All threads must call it.
+__device__ __forceinline__ bool grid_sync(GridBarrier* bar, unsigned int rank, unsigned int size,
+                                          unsigned long long limit_ns, int* err) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
+    const unsigned int add = rank == 0 ? 0x80000000u - (size - 1) : 1u;
+    __threadfence();
+    const unsigned int old = atom_add_acq_rel_gpu(&bar->count, add);
     int ok = 1;
-    const unsigned int g = ld_acquire_gpu(&bar->gen);
-    __threadfence();
-    const unsigned int arrived = atomicAdd(&bar->count, 1u);
-    if (arrived == nblocks - 1) {
-      atomicExch(&bar->count, 0u);
-      red_release_gpu_add(&bar->gen, 1u);
-    } else {
-      ok = bounded_wait_change(&bar->gen, g, limit_ns, err) ? 1 : 0;
+    const unsigned long long t0 = globaltimer_ns();
+    unsigned int spins = 0;
+    while (((ld_acquire_gpu(&bar->count) ^ old) & 0x80000000u) == 0) {
+      if ((++spins & 15u) == 0) {
+        if (*(volatile int*)err != 0) { ok = 0; break; }
+        if (globaltimer_ns() - t0 > limit_ns) {
+          atomicCAS(err, 0, (int)SSSP_ERR_TIMEOUT);
+          ok = 0;
+          break;
+        }
+      }
     }
-    __threadfence();
-    if (*(volatile int*)err != 0) ok = 0;
     s_ok = ok;
   }
   __syncthreads();

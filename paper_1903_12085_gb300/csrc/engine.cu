@@ -1,35 +1,43 @@
 // engine.cu -- the phase engine of the generic phased SSSP algorithm (Section 3).
 //
-// One persistent launch runs a whole solve.  Every phase is three steps
-// separated by group barriers (a bounded grid barrier for a single solve, the
-// block barrier for the batched solver):
+// One persistent launch runs a whole solve (or, for batches, each group of
+// blocks runs whole solves one after another).  A phase settles every fringe
+// vertex that the criterion proves final, against the state at the start of
+// the phase, then relaxes all of their out-edges:
 //
-//   A  thresholds   minD   = min_{u in F} d[u]
-//                   minOut = min_{u in F} d[u] + outmin(u)          (OUT criteria)
-//                   warp shuffle -> block -> one 64-bit atomicMin per block.
-//                   For the dynamic (SIMPLE) criteria the per-vertex cursors into
-//                   the cost-sorted rows are first advanced past settled endpoints
-//                   (Proposition 3: the minimum over the remaining edges is the
-//                   first live element of the presorted list).
-//   B  select       v in F is settled iff
-//                     IN : d[v] <= minD + inmin(v)   (inmin empty -> holds)
-//                     OUT: d[v] <= minOut
-//                   (eqs. crit:instatic / crit:insimple / crit:outstatic /
-//                   crit:outsimple), all against the phase-start state.  Settled
-//                   vertices are marked S before any relaxation; those with
-//                   out-edges go to the relax list with an exclusive prefix of
-//                   their degrees (one packed 64-bit atomicAdd per warp reserves
-//                   both the slots and the edge range, so the prefix is monotone);
-//                   the rest of F is compacted into the next queue.
-//   C  relax        edge-balanced over the relax list: each block takes a tile of
-//                   consecutive edges, finds the owning settled vertices by binary
-//                   search, and for every edge (u,t) with t not in S does
-//                   cand = d[u] + c(u,t); if cand < d[t]: atomicMin(d[t], cand); a
-//                   vertex whose old value was infinite moves U -> F (appended).
+//   select   v in F is settled iff                          (step B)
+//              IN : d[v] <= minD + inmin(v)     (inmin empty -> holds)
+//              OUT: d[v] <= minOut
+//            (eqs. crit:instatic / crit:insimple / crit:outstatic /
+//            crit:outsimple).  Settled vertices are marked S before any
+//            relaxation; those with out-edges go to the relax list with an
+//            exclusive prefix of their degrees (one packed 64-bit atomicAdd per
+//            warp reserves the slots and the edge range together, so the prefix
+//            is monotone); the rest of F is compacted into the next queue.
+//   relax    edge-balanced over the relax list: a block takes a tile of
+//            consecutive edges, finds the owners by binary search, and for every
+//            edge (u,t) with t not in S: cand = d[u] + c(u,t); if cand < d[t]:
+//            atomicMin(d[t], cand); an old value of infinity moves t U -> F.
+//
+// Thresholds minD = min_F d and minOut = min_F (d + outmin) come either
+//   - fused (two barriers per phase): the values of phase k+1 are accumulated
+//     during phase k from the kept fringe entries (step B) and from every
+//     relaxation that lowered a distance (step C).  The final d of every
+//     vertex of the next fringe is among the accumulated values and every
+//     accumulated value is >= its vertex's final d, so the minima are exact.
+//     Used when the OUT minimum is static (it never changes for a vertex).
+//     With IN-SIMPLE the in-cursor of every target of a relaxed edge is
+//     advanced in step C, so the dynamic in-minima are exact for the next phase.
+//   - or by a separate pass (step A, three barriers) that also advances the
+//     out-/in-cursors lazily over the cost-sorted rows (Proposition 3): needed
+//     by OUT-SIMPLE (out-minima grow when a target settles) and DIJK.
+//
+// Solo mode: while |F| is small, block 0 of the group runs whole phases alone
+// with block barriers (tens of ns instead of ~1 us per grid barrier); the other
+// blocks wait on a bounded gate and rejoin when |F| grows or the solve ends.
 //
 // Phase control: the phase that settles the source is phase 1; the loop ends
-// when the next queue is empty.  The frontier is either the compacted queue
-// (sparse) or a scan of the status array (dense); both keep the queue exact.
+// when the next queue is empty.
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -39,33 +47,37 @@
 
 namespace sssp {
 
-struct GridGroup {
+// A group of co-resident blocks running one solve.  size == 1: block barriers.
+struct Grp {
   GridBarrier* bar;
   int* err;
   unsigned long long limit;
-  __device__ unsigned int rank() const { return blockIdx.x; }
-  __device__ unsigned int size() const { return gridDim.x; }
-  __device__ bool sync() const { return grid_sync(bar, gridDim.x, limit, err); }
-};
-
-struct BlockGroup {
-  __device__ unsigned int rank() const { return 0; }
-  __device__ unsigned int size() const { return 1; }
+  unsigned int rank;
+  unsigned int size;
   __device__ bool sync() const {
-    __syncthreads();
-    return true;
+    if (size == 1) {
+      __syncthreads();
+      return true;
+    }
+    return grid_sync(bar, rank, size, limit, err);
   }
 };
 
-// Number of elements <= x in the strictly increasing array a[0..len), by one
-// warp (31 pivots per round).  All 32 lanes must call it; every lane gets the result.
-__device__ __forceinline__ uint32_t warp_upper_bound(const uint32_t* a, uint32_t len, uint32_t x) {
+// Per-phase choice: which IN variant and which fringe representation.
+struct Arm {
+  bool in_simple;
+  bool dense;
+};
+
+// Number of relax-list entries whose base is <= x (bases strictly increasing),
+// by one warp with 31 pivots per round.  All 32 lanes call it.
+__device__ __forceinline__ uint32_t warp_upper_bound_sp(const SpEnt* a, uint32_t len, uint32_t x) {
   const int lane = threadIdx.x & 31;
   uint32_t lo = 0, hi = len;
   while (hi - lo > 32) {
     const uint32_t span = hi - lo;
     const uint32_t p = lo + (uint32_t)(((uint64_t)span * (uint32_t)(lane + 1)) >> 5);
-    const bool le = lane < 31 && ldcg_u32(a + p) <= x;
+    const bool le = lane < 31 && ldcg_u32(&a[p].base) <= x;
     const unsigned int mask = __ballot_sync(0xFFFFFFFFu, le);
     const int c = __popc(mask);
     const uint32_t plo = __shfl_sync(0xFFFFFFFFu, p, c > 0 ? c - 1 : 0);
@@ -73,7 +85,7 @@ __device__ __forceinline__ uint32_t warp_upper_bound(const uint32_t* a, uint32_t
     if (c > 0) lo = plo + 1;
     if (c < 31) hi = phi;
   }
-  const bool le = lo + lane < hi && ldcg_u32(a + lo + lane) <= x;
+  const bool le = lo + lane < hi && ldcg_u32(&a[lo + lane].base) <= x;
   return lo + __popc(__ballot_sync(0xFFFFFFFFu, le));
 }
 
@@ -81,8 +93,7 @@ __device__ __forceinline__ uint32_t warp_upper_bound(const uint32_t* a, uint32_t
 __device__ __forceinline__ uint32_t out_min_dynamic(const GraphView& g, const SolveWS& w, uint32_t v) {
   const uint32_t c0 = ldcg_u32(&w.cur_out[v]);
   const uint32_t end = (uint32_t)__ldg(&g.row_off[v + 1]);
-  uint32_t c = c0;
-  uint32_t cost = kInf32;
+  uint32_t c = c0, cost = kInf32;
   while (c < end) {
     const uint2 e = __ldg(&g.edges[c]);
     if (ldcg_u8(&w.status[e.x]) != kS) { cost = e.y; break; }
@@ -92,277 +103,421 @@ __device__ __forceinline__ uint32_t out_min_dynamic(const GraphView& g, const So
   return cost;
 }
 
-// Advance the in-cursor of v past sources in S (result read back in step B).
-__device__ __forceinline__ void in_cursor_advance(const GraphView& g, const SolveWS& w, uint32_t v) {
+// Advance the in-cursor of v past sources in S; return the dynamic in-minimum.
+// Concurrent callers for the same v compute the same position (S does not
+// change while they run), published with atomicMax.
+__device__ __forceinline__ uint32_t in_min_dynamic(const GraphView& g, const SolveWS& w, uint32_t v, bool shared_v) {
   const uint32_t c0 = ldcg_u32(&w.cur_in[v]);
   const uint32_t end = (uint32_t)__ldg(&g.rrow_off[v + 1]);
-  uint32_t c = c0;
-  while (c < end && ldcg_u8(&w.status[__ldg(&g.redges[c]).x]) == kS) ++c;
-  if (c != c0) w.cur_in[v] = c;
+  uint32_t c = c0, cost = kInf32;
+  while (c < end) {
+    const uint2 e = __ldg(&g.redges[c]);
+    if (ldcg_u8(&w.status[e.x]) != kS) { cost = e.y; break; }
+    ++c;
+  }
+  if (c != c0) {
+    if (shared_v) atomicMax(&w.cur_in[v], c);
+    else w.cur_in[v] = c;
+  }
+  return cost;
 }
 
-__device__ __forceinline__ uint32_t in_min_dynamic(const GraphView& g, const SolveWS& w, uint32_t v) {
-  const uint32_t c = ldcg_u32(&w.cur_in[v]);
-  return c < (uint32_t)__ldg(&g.rrow_off[v + 1]) ? __ldg(&g.redges[c]).y : kInf32;
+struct Shared {
+  unsigned long long* red;  // 64
+  uint32_t* s_base;         // kTile
+  uint32_t* s_row;          // kTile
+  unsigned long long* s_d;  // kTile
+  uint32_t* s_range;        // 2
+};
+
+__device__ __forceinline__ Shared carve(unsigned char* smem) {
+  Shared s;
+  s.red = reinterpret_cast<unsigned long long*>(smem);
+  s.s_d = s.red + 64;
+  s.s_base = reinterpret_cast<uint32_t*>(s.s_d + kTile);
+  s.s_row = s.s_base + kTile;
+  s.s_range = s.s_row + kTile;
+  return s;
 }
 
-template <class G>
-__device__ void solve_body(const SolveParams& p, const G& grp, unsigned char* smem) {
+// Solve-wide constants derived from the criterion mask.
+struct Mode {
+  bool fused;        // thresholds accumulated in B and C
+  bool use_in;       // some IN criterion
+  bool in_maintain;  // dynamic in-minima kept exact in step C (fused kind)
+  bool use_out;
+  bool out_dyn;      // OUT-SIMPLE (three-step kind)
+  bool dijk;
+};
+
+__device__ __forceinline__ Mode mode_of(uint32_t crit, bool has_cur_in) {
+  Mode m;
+  m.out_dyn = (crit & SSSP_OUT_SIMPLE) != 0;
+  m.use_out = m.out_dyn || (crit & SSSP_OUT_STATIC) != 0;
+  m.dijk = (crit & SSSP_DIJK) != 0;
+  m.fused = !m.out_dyn && !m.dijk;
+  const bool policy = (crit & SSSP_POLICY_LEARNED) != 0;
+  m.use_in = (crit & (SSSP_IN_STATIC | SSSP_IN_SIMPLE)) != 0 || policy;
+  m.in_maintain = m.fused && has_cur_in && ((crit & SSSP_IN_SIMPLE) != 0 || policy);
+  return m;
+}
+
+// ---------------------------------------------------------------------------
+// One phase, run by every block of the group.  Returns false if a barrier gave up.
+__device__ bool run_phase(const SolveParams& p, const Grp& grp, const Mode& md, const Arm arm, uint64_t k,
+                          const Shared& sh) {
   const GraphView& g = p.g;
   const SolveWS& w = p.ws;
   Ctl* ctl = w.ctl;
   const uint32_t n = g.n;
   const unsigned int tid = threadIdx.x, nthr = blockDim.x;
   const unsigned int lane = tid & 31, warp = tid >> 5;
-  const uint64_t grank = grp.rank(), gsize = grp.size();
-  const uint64_t gthreads = gsize * nthr;
-  const uint64_t gtid = grank * nthr + tid;
-  const bool leader = grank == 0 && tid == 0;
+  const uint64_t gthreads = (uint64_t)grp.size * nthr;
+  const uint64_t gtid = (uint64_t)grp.rank * nthr + tid;
+  const bool leader = grp.rank == 0 && tid == 0;
+  const int cur = (int)((k - 1) & 1);
+  const uint32_t* Q = w.q[cur];
+  uint32_t* Qn = w.q[cur ^ 1];
+  PhaseSlot* S0 = &ctl->slot[k % 3];
+  PhaseSlot* S1 = &ctl->slot[(k + 1) % 3];
+  const uint32_t nF = ldcg_u32(&S0->qcount);
+  const bool dense = arm.dense;
+  // dynamic in-minimum used in this phase's selection
+  const bool in_dyn = md.use_in && arm.in_simple && w.cur_in != nullptr;
+  unsigned long long t0 = 0;
+  if (leader) {
+    t0 = globaltimer_ns();
+    PhaseSlot* S2 = &ctl->slot[(k + 2) % 3];
+    S2->min_d = S2->min_out = kInf64;
+    S2->a_min_d = S2->a_min_out = kInf64;
+    S2->relax_packed = 0;
+    S2->qcount = 0;
+    S2->argmin = kInf32;
+    S2->settled_now = 0;
+    ctl->sum_f += nF;
+  }
 
-  unsigned long long* red = reinterpret_cast<unsigned long long*>(smem);
-  uint32_t* s_base = reinterpret_cast<uint32_t*>(smem + 64 * sizeof(unsigned long long));
-  unsigned long long* s_row = reinterpret_cast<unsigned long long*>(s_base + kTile);
-  unsigned long long* s_d = s_row + kTile;
-  uint32_t* s_range = reinterpret_cast<uint32_t*>(s_d + kTile);
+  // ---- thresholds
+  unsigned long long minD, minOut;
+  if (md.fused) {
+    minD = ldcg_u64(&S0->min_d);
+    minOut = ldcg_u64(&S0->min_out);
+  } else {
+    // A: thresholds over the phase-start state, advancing cursors lazily
+    unsigned long long lmin_d = kInf64, lmin_out = kInf64;
+    auto visit = [&](uint32_t v) {
+      const unsigned long long dv = ldcg_u64(&w.vrec[v].d);
+      lmin_d = dv < lmin_d ? dv : lmin_d;
+      if (md.use_out) {
+        const uint32_t om = md.out_dyn ? out_min_dynamic(g, w, v) : __ldg(&g.out_min[v]);
+        if (om != kInf32) {
+          const unsigned long long x = dv + om;
+          lmin_out = x < lmin_out ? x : lmin_out;
+        }
+      }
+      if (in_dyn) w.vrec[v].im = in_min_dynamic(g, w, v, false);
+    };
+    if (dense) {
+      for (uint64_t v = gtid; v < n; v += gthreads)
+        if (ldcg_u8(&w.status[v]) == kF) visit((uint32_t)v);
+    } else {
+      for (uint64_t i = gtid; i < nF; i += gthreads) visit(ldcg_u32(&Q[i]));
+    }
+    block_min2_to_global(lmin_d, lmin_out, &S0->a_min_d, md.use_out ? &S0->a_min_out : nullptr, sh.red);
+    if (!grp.sync()) return false;
+    minD = ldcg_u64(&S0->a_min_d);
+    minOut = ldcg_u64(&S0->a_min_out);
+  }
+  uint32_t amin = kInf32;
+  if (md.dijk) {  // DIJK: the lowest id among fringe vertices of minimum d
+    uint32_t lid = kInf32;
+    if (dense) {
+      for (uint64_t v = gtid; v < n; v += gthreads)
+        if (ldcg_u8(&w.status[v]) == kF && ldcg_u64(&w.vrec[v].d) == minD) lid = min(lid, (uint32_t)v);
+    } else {
+      for (uint64_t i = gtid; i < nF; i += gthreads) {
+        const uint32_t v = ldcg_u32(&Q[i]);
+        if (ldcg_u64(&w.vrec[v].d) == minD) lid = min(lid, v);
+      }
+    }
+    lid = __reduce_min_sync(0xFFFFFFFFu, lid);
+    if (lane == 0 && lid != kInf32) atomicMin(&S0->argmin, lid);
+    if (!grp.sync()) return false;
+    amin = ldcg_u32(&S0->argmin);
+  }
 
-  const uint32_t crit = p.crit;
-  const bool in_dyn = (crit & SSSP_IN_SIMPLE) != 0;
-  const bool in_st = !in_dyn && (crit & SSSP_IN_STATIC) != 0;
-  const bool use_in = in_dyn || in_st;
-  const bool out_dyn = (crit & SSSP_OUT_SIMPLE) != 0;
-  const bool use_out = out_dyn || (crit & SSSP_OUT_STATIC) != 0;
-  const bool dijk = (crit & SSSP_DIJK) != 0;
+  // ---- B: select S', mark settled, build the relax list, compact the rest of F
+  unsigned long long pd = kInf64, po = kInf64;  // fused partials for phase k+1
+  {
+    const uint64_t total = dense ? n : nF;
+    uint32_t settled_here = 0;
+    for (uint64_t base = gtid & ~31ull; base < total; base += gthreads) {
+      const uint64_t i = base + lane;
+      bool valid = i < total;
+      uint32_t v = 0;
+      if (valid) {
+        v = dense ? (uint32_t)i : ldcg_u32(&Q[i]);
+        if (dense) valid = ldcg_u8(&w.status[v]) == kF;
+      }
+      bool sel = false;
+      uint32_t deg = 0, row = 0;
+      unsigned long long dv = 0;
+      if (valid) {
+        const VRec r = ldcg_vrec(&w.vrec[v]);
+        dv = r.d;
+        if (md.use_in) {
+          // record im is the dynamic minimum when maintained, else the static one
+          const uint32_t im = (in_dyn || !md.in_maintain) ? r.im : __ldg(&g.in_min[v]);
+          sel = (im == kInf32) || dv <= minD + im;
+        }
+        if (!sel && md.use_out) sel = dv <= minOut;
+        if (!sel && md.dijk) sel = (v == amin);
+        if (sel) {
+          w.status[v] = kS;
+          if (w.settle_phase) w.settle_phase[v] = (uint32_t)k;
+          const uint64_t r0 = __ldg(&g.row_off[v]);
+          row = (uint32_t)r0;
+          deg = (uint32_t)(__ldg(&g.row_off[v + 1]) - r0);
+        } else if (md.fused) {
+          pd = dv < pd ? dv : pd;
+          if (r.om != kInf32) {
+            const unsigned long long x = dv + r.om;
+            po = x < po ? x : po;
+          }
+        }
+      }
+      // relax list (settled vertices with out-edges): slots and edge range in one atomic
+      const bool rl = sel && deg > 0;
+      const unsigned int rmask = __ballot_sync(0xFFFFFFFFu, rl);
+      if (rmask) {
+        const uint32_t c = rl ? deg : 0;
+        const uint32_t incl = warp_inclusive_scan(c);
+        const uint32_t tot = __shfl_sync(0xFFFFFFFFu, incl, 31);
+        unsigned long long old = 0;
+        if (lane == 0) old = atomicAdd(&S0->relax_packed, ((unsigned long long)__popc(rmask) << 32) | tot);
+        old = __shfl_sync(0xFFFFFFFFu, old, 0);
+        if (rl) {
+          const uint32_t slot = (uint32_t)(old >> 32) + __popc(rmask & ((1u << lane) - 1u));
+          if (slot < n) {
+            const uint32_t base_e = (uint32_t)old + incl - c;
+            *reinterpret_cast<ulonglong2*>(&w.sp[slot]) =
+                make_ulonglong2(dv, (unsigned long long)row | ((unsigned long long)base_e << 32));
+          } else {
+            atomicCAS(&ctl->err, 0, (int)SSSP_ERR_INTERNAL);
+          }
+        }
+      }
+      warp_append(Qn, &S1->qcount, valid && !sel, v, n, &ctl->err);
+      settled_here += __popc(__ballot_sync(0xFFFFFFFFu, sel));
+    }
+    if (lane == 0 && settled_here) atomicAdd(&S0->settled_now, settled_here);
+  }
+  if (md.fused) block_min2_to_global(pd, po, &S1->min_d, md.use_out ? &S1->min_out : nullptr, sh.red);
+  if (!grp.sync()) return false;
 
-  // ---- initialisation: d = inf, all vertices unexplored, cursors at row starts
+  // ---- C: relax every out-edge of S' (edge-balanced tiles)
+  pd = kInf64;
+  po = kInf64;
+  const unsigned long long packed = ldcg_u64(&S0->relax_packed);
+  const uint32_t nS = (uint32_t)(packed >> 32);
+  const uint32_t E = (uint32_t)packed;
+  for (uint64_t tile = grp.rank; tile * kTile < E; tile += grp.size) {
+    const uint32_t e0 = (uint32_t)(tile * kTile);
+    const uint32_t e1 = (uint64_t)e0 + kTile < E ? e0 + kTile : E;
+    if (warp == 0) {
+      uint32_t lo = 0, hi = nS - 1;
+      if (!(e0 == 0 && e1 == E)) {
+        lo = warp_upper_bound_sp(w.sp, nS, e0) - 1;
+        hi = warp_upper_bound_sp(w.sp, nS, e1 - 1) - 1;
+      }
+      if (lane == 0) { sh.s_range[0] = lo; sh.s_range[1] = hi; }
+    }
+    __syncthreads();
+    const uint32_t lo = sh.s_range[0], cnt = sh.s_range[1] - sh.s_range[0] + 1;
+    for (uint32_t j = tid; j < cnt; j += nthr) {
+      const SpEnt e = ldcg_sp(&w.sp[lo + j]);
+      sh.s_base[j] = e.base;
+      sh.s_row[j] = e.row;
+      sh.s_d[j] = e.d;
+    }
+    __syncthreads();
+    for (uint32_t eb = e0 + warp * 32; eb < e1; eb += nthr) {
+      const uint32_t e = eb + lane;
+      bool fresh = false;
+      uint32_t t = 0;
+      if (e < e1) {
+        uint32_t a = 0, b = cnt;  // owner = last j with s_base[j] <= e
+        while (b - a > 1) {
+          const uint32_t mid = (a + b) >> 1;
+          if (sh.s_base[mid] <= e) a = mid; else b = mid;
+        }
+        const uint2 ed = __ldg(&g.edges[sh.s_row[a] + (e - sh.s_base[a])]);
+        t = ed.x;
+        if (ldcg_u8(&w.status[t]) != kS) {
+          const VRec rt = ldcg_vrec(&w.vrec[t]);
+          const unsigned long long cand = sh.s_d[a] + ed.y;
+          if (cand < rt.d) {
+            const unsigned long long old = atomicMin(&w.vrec[t].d, cand);
+            if (old == kInf64) {
+              w.status[t] = kF;
+              fresh = true;
+            }
+            if (md.fused && cand < old) {
+              pd = cand < pd ? cand : pd;
+              if (rt.om != kInf32) {
+                const unsigned long long x = cand + rt.om;
+                po = x < po ? x : po;
+              }
+            }
+          }
+          if (md.in_maintain) {
+            const uint32_t im = in_min_dynamic(g, w, t, true);
+            if (im != rt.im) w.vrec[t].im = im;
+          }
+        }
+      }
+      warp_append(Qn, &S1->qcount, fresh, t, n, &ctl->err);
+    }
+    __syncthreads();
+  }
+  if (md.fused) block_min2_to_global(pd, po, &S1->min_d, md.use_out ? &S1->min_out : nullptr, sh.red);
+  if (leader) ctl->relaxed += E;
+  if (!grp.sync()) return false;
+  if (leader) {
+    const uint32_t settled_now = ldcg_u32(&S0->settled_now);
+    ctl->settled += settled_now;
+    ctl->phases = k;
+    if (w.trace && k <= w.trace_cap) {
+      sssp_phase_record r;
+      r.frontier = nF;
+      r.settled = settled_now;
+      r.min_d = minD;
+      r.min_out = md.use_out ? minOut : kInf64;
+      r.deg_settled = E;
+      uint32_t c = p.crit & SSSP_CRITERIA_MASK;
+      if (md.use_in) c = (c & ~(uint32_t)(SSSP_IN_STATIC | SSSP_IN_SIMPLE)) | (in_dyn ? SSSP_IN_SIMPLE : SSSP_IN_STATIC);
+      r.criterion = c;
+      r.arm = (dense ? 1u : 0u) | (grp.size == 1 ? 2u : 0u);
+      r.t_start_ns = t0;
+      r.t_end_ns = globaltimer_ns();
+      r.reserved = 0;
+      w.trace[k - 1] = r;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ Arm arm_for(const SolveParams& p, uint32_t nF) {
+  Arm a;
+  a.in_simple = (p.crit & SSSP_IN_SIMPLE) != 0;
+  a.dense = (p.crit & SSSP_FRONTIER_DENSE) != 0 || ((p.crit & SSSP_FRONTIER_AUTO) && nF > (p.g.n >> 2));
+  return a;
+}
+
+// Initialise, run all phases (switching to solo mode while |F| is small),
+// write the distances.  Every block of the group calls it.
+__device__ void solve_body(const SolveParams& p, const Grp& grp, unsigned char* smem) {
+  const GraphView& g = p.g;
+  const SolveWS& w = p.ws;
+  Ctl* ctl = w.ctl;
+  const uint32_t n = g.n;
+  const unsigned int tid = threadIdx.x, nthr = blockDim.x;
+  const uint64_t gthreads = (uint64_t)grp.size * nthr;
+  const uint64_t gtid = (uint64_t)grp.rank * nthr + tid;
+  const bool leader = grp.rank == 0 && tid == 0;
+  const Shared sh = carve(smem);
+  const Mode md = mode_of(p.crit, w.cur_in != nullptr);
+
   for (uint64_t v = gtid; v < n; v += gthreads) {
-    w.d[v] = kInf64;
+    const uint32_t im = __ldg(&g.in_min[v]), om = __ldg(&g.out_min[v]);
+    *reinterpret_cast<ulonglong2*>(&w.vrec[v]) =
+        make_ulonglong2(kInf64, (unsigned long long)im | ((unsigned long long)om << 32));
     w.status[v] = kU;
     if (w.cur_out) w.cur_out[v] = (uint32_t)g.row_off[v];
     if (w.cur_in) w.cur_in[v] = (uint32_t)g.rrow_off[v];
     if (w.settle_phase) w.settle_phase[v] = 0;
   }
   if (leader) {
-    ctl->min_d[0] = ctl->min_d[1] = kInf64;
-    ctl->min_out[0] = ctl->min_out[1] = kInf64;
-    ctl->argmin[0] = ctl->argmin[1] = kInf32;
-    ctl->qcount[0] = 1;
-    ctl->qcount[1] = 0;
+    for (int j = 0; j < 3; ++j) {
+      PhaseSlot* s = &ctl->slot[j];
+      s->min_d = s->min_out = s->a_min_d = s->a_min_out = kInf64;
+      s->relax_packed = 0;
+      s->qcount = 0;
+      s->argmin = kInf32;
+      s->settled_now = 0;
+    }
     ctl->phases = ctl->sum_f = ctl->settled = ctl->relaxed = 0;
+    ctl->heartbeat = 0;
+    ctl->next_phase = 0;
   }
   if (!grp.sync()) return;
   if (leader) {
-    w.d[p.source] = 0;
+    w.vrec[p.source].d = 0;
     w.status[p.source] = kF;
     w.q[0][0] = p.source;
+    PhaseSlot* s1 = &ctl->slot[1];
+    s1->qcount = 1;
+    s1->min_d = 0;
+    const uint32_t om = __ldg(&g.out_min[p.source]);
+    s1->min_out = om == kInf32 ? kInf64 : (unsigned long long)om;
   }
   if (!grp.sync()) return;
 
-  uint64_t phase = 1;
-  for (;; ++phase) {
-    const int cur = (int)((phase - 1) & 1), nxt = cur ^ 1;
-    const uint32_t nF = ldcg_u32(&ctl->qcount[cur]);
+  unsigned int episodes = 0;
+  uint64_t k = 1;
+  for (;;) {
+    uint32_t nF = ldcg_u32(&ctl->slot[k % 3].qcount);
     if (nF == 0) break;
-    const bool dense = (crit & SSSP_FRONTIER_DENSE) || ((crit & SSSP_FRONTIER_AUTO) && nF > (n >> 3));
-    const uint32_t* Q = w.q[cur];
-    uint32_t* Qn = w.q[nxt];
-    unsigned long long t0 = 0;
-    if (leader) {
-      t0 = globaltimer_ns();
-      ctl->qcount[nxt] = 0;
-      ctl->relax_packed = 0;
-      ctl->settled_now = 0;
-      ctl->min_d[nxt] = kInf64;
-      ctl->min_out[nxt] = kInf64;
-      ctl->argmin[nxt] = kInf32;
-      ctl->sum_f += nF;
-    }
-
-    // ---- A: thresholds over the phase-start state
-    {
-      unsigned long long lmin_d = kInf64, lmin_out = kInf64;
-      auto visit = [&](uint32_t v) {
-        const unsigned long long dv = ldcg_u64(&w.d[v]);
-        lmin_d = dv < lmin_d ? dv : lmin_d;
-        if (use_out) {
-          const uint32_t om = out_dyn ? out_min_dynamic(g, w, v) : __ldg(&g.out_min[v]);
-          if (om != kInf32) {
-            const unsigned long long k = dv + om;
-            lmin_out = k < lmin_out ? k : lmin_out;
-          }
+    if (grp.size > 1 && nF <= p.solo_max) {
+      __shared__ unsigned long long s_next;
+      __shared__ int s_ok;
+      if (grp.rank == 0) {
+        // block 0 alone, block barriers, until |F| grows or the solve ends
+        const Grp solo{grp.bar, grp.err, grp.limit, 0, 1};
+        bool ok = true;
+        while (nF != 0 && nF <= p.solo_max) {
+          if (!run_phase(p, solo, md, arm_for(p, nF), k, sh)) { ok = false; break; }
+          ++k;
+          if (tid == 0) ctl->heartbeat = k;
+          nF = ldcg_u32(&ctl->slot[k % 3].qcount);
         }
-        if (in_dyn) in_cursor_advance(g, w, v);
-      };
-      if (dense) {
-        for (uint64_t v = gtid; v < n; v += gthreads)
-          if (ldcg_u8(&w.status[v]) == kF) visit((uint32_t)v);
+        __syncthreads();
+        if (tid == 0) {
+          ctl->next_phase = k;
+          __threadfence();
+          red_release_gpu_add(&ctl->gate, 1u);
+        }
+        __syncthreads();
+        if (!ok) return;
       } else {
-        for (uint64_t i = gtid; i < nF; i += gthreads) visit(ldcg_u32(&Q[i]));
-      }
-      block_min2_to_global(lmin_d, lmin_out, &ctl->min_d[cur], use_out ? &ctl->min_out[cur] : nullptr, red);
-    }
-    if (!grp.sync()) return;
-    const unsigned long long minD = ldcg_u64(&ctl->min_d[cur]);
-    const unsigned long long minOut = use_out ? ldcg_u64(&ctl->min_out[cur]) : 0;
-
-    uint32_t amin = kInf32;
-    if (dijk) {  // DIJK: the lowest id among vertices of minimum d
-      uint32_t lid = kInf32;
-      if (dense) {
-        for (uint64_t v = gtid; v < n; v += gthreads)
-          if (ldcg_u8(&w.status[v]) == kF && ldcg_u64(&w.d[v]) == minD) lid = min(lid, (uint32_t)v);
-      } else {
-        for (uint64_t i = gtid; i < nF; i += gthreads) {
-          const uint32_t v = ldcg_u32(&Q[i]);
-          if (ldcg_u64(&w.d[v]) == minD) lid = min(lid, v);
+        if (tid == 0) {
+          s_ok = bounded_wait_change(&ctl->gate, episodes, grp.limit, grp.err, &ctl->heartbeat) ? 1 : 0;
+          s_next = ld_relaxed_gpu_u64(&ctl->next_phase);
         }
+        __syncthreads();
+        if (!s_ok) return;
+        k = s_next;
+        __syncthreads();
       }
-      lid = __reduce_min_sync(0xFFFFFFFFu, lid);
-      if (lane == 0 && lid != kInf32) atomicMin(&ctl->argmin[cur], lid);
-      if (!grp.sync()) return;
-      amin = ldcg_u32(&ctl->argmin[cur]);
+      ++episodes;
+      continue;
     }
-
-    // ---- B: select S', mark settled, build relax list, compact the rest of F
-    {
-      const uint64_t total = dense ? n : nF;
-      uint32_t settled_here = 0;
-      for (uint64_t base = gtid & ~31ull; base < total; base += gthreads) {
-        const uint64_t i = base + lane;
-        bool valid = i < total;
-        uint32_t v = 0;
-        if (valid) {
-          v = dense ? (uint32_t)i : ldcg_u32(&Q[i]);
-          if (dense) valid = ldcg_u8(&w.status[v]) == kF;
-        }
-        bool sel = false;
-        uint32_t deg = 0;
-        if (valid) {
-          const unsigned long long dv = ldcg_u64(&w.d[v]);
-          if (use_in) {
-            const uint32_t im = in_dyn ? in_min_dynamic(g, w, v) : __ldg(&g.in_min[v]);
-            sel = (im == kInf32) || dv <= minD + im;
-          }
-          if (!sel && use_out) sel = dv <= minOut;
-          if (!sel && dijk) sel = (v == amin);
-          if (sel) {
-            w.status[v] = kS;
-            if (w.settle_phase) w.settle_phase[v] = (uint32_t)phase;
-            deg = (uint32_t)(__ldg(&g.row_off[v + 1]) - __ldg(&g.row_off[v]));
-          }
-        }
-        // relax list (settled vertices with out-edges): slots and edge range in one atomic
-        const bool rl = sel && deg > 0;
-        const unsigned int rmask = __ballot_sync(0xFFFFFFFFu, rl);
-        if (rmask) {
-          const uint32_t c = rl ? deg : 0;
-          const uint32_t incl = warp_inclusive_scan(c);
-          const uint32_t tot = __shfl_sync(0xFFFFFFFFu, incl, 31);
-          unsigned long long old = 0;
-          if (lane == 0) old = atomicAdd(&ctl->relax_packed, ((unsigned long long)__popc(rmask) << 32) | tot);
-          old = __shfl_sync(0xFFFFFFFFu, old, 0);
-          if (rl) {
-            const uint32_t slot = (uint32_t)(old >> 32) + __popc(rmask & ((1u << lane) - 1u));
-            if (slot < n) {
-              w.sp_v[slot] = v;
-              w.sp_base[slot] = (uint32_t)old + incl - c;
-            } else {
-              atomicCAS(&ctl->err, 0, (int)SSSP_ERR_INTERNAL);
-            }
-          }
-        }
-        warp_append(Qn, &ctl->qcount[nxt], valid && !sel, v, n, &ctl->err);
-        settled_here += __popc(__ballot_sync(0xFFFFFFFFu, sel));
-      }
-      if (lane == 0 && settled_here) atomicAdd(&ctl->settled_now, settled_here);
-    }
-    if (!grp.sync()) return;
-
-    // ---- C: relax every out-edge of S' (edge-balanced tiles)
-    const unsigned long long packed = ldcg_u64(&ctl->relax_packed);
-    const uint32_t nS = (uint32_t)(packed >> 32);
-    const uint32_t E = (uint32_t)packed;
-    for (uint64_t tile = grank; tile * kTile < E; tile += gsize) {
-      const uint32_t e0 = (uint32_t)(tile * kTile);
-      const uint32_t e1 = (uint64_t)e0 + kTile < E ? e0 + kTile : E;
-      if (warp == 0) {
-        uint32_t lo = 0, hi = nS - 1;
-        if (!(e0 == 0 && e1 == E)) {
-          lo = warp_upper_bound(w.sp_base, nS, e0) - 1;
-          hi = warp_upper_bound(w.sp_base, nS, e1 - 1) - 1;
-        }
-        if (lane == 0) { s_range[0] = lo; s_range[1] = hi; }
-      }
-      __syncthreads();
-      const uint32_t lo = s_range[0], cnt = s_range[1] - s_range[0] + 1;
-      for (uint32_t k = tid; k < cnt; k += nthr) {
-        const uint32_t v = ldcg_u32(&w.sp_v[lo + k]);
-        s_base[k] = ldcg_u32(&w.sp_base[lo + k]);
-        s_row[k] = __ldg(&g.row_off[v]);
-        s_d[k] = ldcg_u64(&w.d[v]);
-      }
-      __syncthreads();
-      for (uint32_t eb = e0 + warp * 32; eb < e1; eb += nthr) {
-        const uint32_t e = eb + lane;
-        bool fresh = false;
-        uint32_t t = 0;
-        if (e < e1) {
-          uint32_t a = 0, b = cnt;  // owner = last k with s_base[k] <= e
-          while (b - a > 1) {
-            const uint32_t mid = (a + b) >> 1;
-            if (s_base[mid] <= e) a = mid; else b = mid;
-          }
-          const uint2 ed = __ldg(&g.edges[s_row[a] + (e - s_base[a])]);
-          t = ed.x;
-          if (ldcg_u8(&w.status[t]) != kS) {
-            const unsigned long long cand = s_d[a] + ed.y;
-            if (cand < ldcg_u64(&w.d[t])) {
-              const unsigned long long old = atomicMin(&w.d[t], cand);
-              if (old == kInf64) {
-                w.status[t] = kF;
-                fresh = true;
-              }
-            }
-          }
-        }
-        warp_append(Qn, &ctl->qcount[nxt], fresh, t, n, &ctl->err);
-      }
-      __syncthreads();
-    }
-    if (leader) {
-      ctl->relaxed += E;
-      ctl->settled += ctl->settled_now;
-    }
-    if (!grp.sync()) return;
-    if (leader && w.trace && phase <= w.trace_cap) {
-      sssp_phase_record r;
-      r.frontier = nF;
-      r.settled = ldcg_u32(&ctl->settled_now);
-      r.min_d = minD;
-      r.min_out = use_out ? minOut : kInf64;
-      r.deg_settled = E;
-      r.criterion = crit & SSSP_CRITERIA_MASK;
-      r.arm = dense ? 1u : 0u;
-      r.t_start_ns = t0;
-      r.t_end_ns = globaltimer_ns();
-      r.reserved = 0;
-      w.trace[phase - 1] = r;
-    }
+    if (!run_phase(p, grp, md, arm_for(p, nF), k, sh)) return;
+    ++k;
   }
-  if (leader) {
-    ctl->phases = phase - 1;
-    __threadfence();
-    ctl->done = 1;
-  }
+  if (!grp.sync()) return;
+  for (uint64_t v = gtid; v < n; v += gthreads) w.dist[v] = ldcg_u64(&w.vrec[v].d);
 }
 
 __global__ void __launch_bounds__(kThreads) k_solve_grid(SolveParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
-  GridGroup grp{&p.ws.ctl->bar, &p.ws.ctl->err, p.wait_ns};
+  const Grp grp{&p.ws.ctl->bar, &p.ws.ctl->err, p.wait_ns, blockIdx.x, gridDim.x};
   solve_body(p, grp, smem);
 }
 
-// Batched solver: each block runs whole solves, pulling the next one from a
-// device counter (descriptors sorted largest first by the host).
+// Batched solver: the grid is split into groups of `bpg` blocks; the first
+// block of a group takes the next solve from a device counter (descriptors
+// sorted largest first by the host) and the group runs it to the end.
 struct BatchItem {
   GraphView g;
   SolveWS ws;
@@ -370,27 +525,43 @@ struct BatchItem {
   uint32_t out_index;  // position of this solve in the caller's arrays
 };
 
+struct GroupSlot {
+  GridBarrier bar;
+  unsigned int item;
+  unsigned int pad;
+};
+
 __global__ void __launch_bounds__(kThreads) k_solve_batch(const BatchItem* items, uint32_t count,
-                                                           unsigned int* next, uint32_t crit,
+                                                           unsigned int* next, GroupSlot* groups, uint32_t bpg,
+                                                           uint32_t crit, uint32_t solo_max,
+                                                           unsigned long long wait_ns, int* err,
                                                            unsigned long long* phases_out) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned int s_item;
+  const unsigned int gidx = blockIdx.x / bpg, rank = blockIdx.x % bpg;
+  GroupSlot* gs = &groups[gidx];
+  const Grp grp{&gs->bar, err, wait_ns, rank, bpg};
   for (;;) {
-    if (threadIdx.x == 0) s_item = atomicAdd(next, 1u);
+    if (rank == 0 && threadIdx.x == 0) gs->item = atomicAdd(next, 1u);
+    if (!grp.sync()) return;
+    if (threadIdx.x == 0) s_item = ldcg_u32(&gs->item);
     __syncthreads();
     const unsigned int it = s_item;
-    __syncthreads();
+    if (!grp.sync()) return;  // everyone has read the mailbox before it is reused
     if (it >= count) break;
     SolveParams p;
     p.g = items[it].g;
     p.ws = items[it].ws;
     p.source = items[it].source;
     p.crit = crit;
-    p.wait_ns = 0;
-    solve_body(p, BlockGroup{}, smem);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      if (p.ws.ctl->err != 0) atomicCAS(&items[0].ws.ctl->err, 0, p.ws.ctl->err);
+    p.wait_ns = wait_ns;
+    p.solo_max = bpg > 1 ? solo_max : 0;
+    p.pad = 0;
+    solve_body(p, grp, smem);
+    if (*(volatile int*)err != 0) return;
+    if (rank == 0 && threadIdx.x == 0) {
+      const int e = (int)ldcg_u32(reinterpret_cast<const uint32_t*>(&p.ws.ctl->err));
+      if (e != 0) atomicCAS(err, 0, e);
       if (phases_out) phases_out[items[it].out_index] = p.ws.ctl->phases;
     }
   }
@@ -408,7 +579,10 @@ sssp_status ensure_kernel_attrs() {
   if (done) return SSSP_OK;
   SSSP_CUDA_TRY(cudaFuncSetAttribute(k_solve_grid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes));
   SSSP_CUDA_TRY(cudaFuncSetAttribute(k_solve_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes));
-  SSSP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_blocks_per_sm, k_solve_grid, kThreads, kSmemBytes));
+  int a = 0, b = 0;
+  SSSP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_solve_grid, kThreads, kSmemBytes));
+  SSSP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_solve_batch, kThreads, kSmemBytes));
+  g_blocks_per_sm = std::min(a, b);
   if (g_blocks_per_sm < 1) return fail(SSSP_ERR_CUDA, "solve kernel cannot be resident");
   done = true;
   return SSSP_OK;
@@ -416,8 +590,9 @@ sssp_status ensure_kernel_attrs() {
 
 sssp_status check_crit(const sssp_graph* g, uint32_t crit) {
   const uint32_t known = SSSP_IN_STATIC | SSSP_OUT_STATIC | SSSP_IN_SIMPLE | SSSP_OUT_SIMPLE | SSSP_DIJK |
-                         SSSP_POLICY_LEARNED | SSSP_FRONTIER_DENSE | SSSP_FRONTIER_AUTO;
+                         SSSP_FRONTIER_DENSE | SSSP_FRONTIER_AUTO;
   if ((crit & SSSP_CRITERIA_MASK) == 0) return fail(SSSP_ERR_INVALID_ARG, "criterion mask has no criterion bit");
+  if (crit & SSSP_POLICY_LEARNED) return fail(SSSP_ERR_UNSUPPORTED, "no phase policy is loaded");
   if (crit & ~known) return fail(SSSP_ERR_INVALID_ARG, "unknown criterion bits 0x%x", crit & ~known);
   if ((crit & SSSP_IN_SIMPLE) && !g->rrow_off)
     return fail(SSSP_ERR_UNSUPPORTED, "IN-SIMPLE needs a graph built with SSSP_GRAPH_REVERSE");
@@ -430,35 +605,46 @@ sssp_status dev_alloc(T** p, size_t count) {
   return SSSP_OK;
 }
 
+// Blocks for a single solve: enough to cover the vertices, at most all
+// co-resident blocks.
+int blocks_for(uint32_t n) {
+  const int max_blocks = g_blocks_per_sm * sm_count();
+  const uint64_t want = grid_blocks() ? grid_blocks() : ((uint64_t)n + kTile - 1) / kTile;
+  return (int)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)max_blocks));
+}
+
 }  // namespace
 
 void workspace_free(Workspace* ws) {
   if (!ws) return;
-  cudaFree(ws->d);
+  cudaFree(ws->vrec);
   cudaFree(ws->status);
   cudaFree(ws->q0);
   cudaFree(ws->q1);
-  cudaFree(ws->sp_v);
-  cudaFree(ws->sp_base);
+  cudaFree(ws->sp);
   cudaFree(ws->cur_out);
   cudaFree(ws->cur_in);
+  cudaFree(ws->dist);
   cudaFree(ws->ctl);
   cudaFreeHost(ws->ctl_host);
   delete ws;
 }
 
-sssp_status workspace_alloc(uint32_t n, bool want_cursors, Workspace** out) {
+sssp_status workspace_alloc(uint32_t n, bool want_cursors, bool want_dist, Workspace** out) {
   Workspace* ws = new (std::nothrow) Workspace();
   if (!ws) return fail(SSSP_ERR_OUT_OF_MEMORY, "host allocation failed");
   ws->n = n;
   sssp_status s = SSSP_OK;
-  if ((s = dev_alloc(&ws->d, n)) || (s = dev_alloc(&ws->status, n)) || (s = dev_alloc(&ws->q0, n)) ||
-      (s = dev_alloc(&ws->q1, n)) || (s = dev_alloc(&ws->sp_v, n)) || (s = dev_alloc(&ws->sp_base, n)) ||
-      (s = dev_alloc(&ws->ctl, 1))) {
+  if ((s = dev_alloc(&ws->vrec, n)) || (s = dev_alloc(&ws->status, n)) || (s = dev_alloc(&ws->q0, n)) ||
+      (s = dev_alloc(&ws->q1, n)) || (s = dev_alloc(&ws->sp, n)) || (s = dev_alloc(&ws->ctl, 1))) {
     workspace_free(ws);
     return s;
   }
   if (want_cursors && ((s = dev_alloc(&ws->cur_out, n)) || (s = dev_alloc(&ws->cur_in, n)))) {
+    workspace_free(ws);
+    return s;
+  }
+  if (want_dist && (s = dev_alloc(&ws->dist, n))) {
     workspace_free(ws);
     return s;
   }
@@ -472,7 +658,7 @@ sssp_status workspace_alloc(uint32_t n, bool want_cursors, Workspace** out) {
 
 sssp_status workspace_get(sssp_graph* g, Workspace** out) {
   if (!g->ws) {
-    sssp_status s = workspace_alloc(g->n, true, &g->ws);
+    sssp_status s = workspace_alloc(g->n, true, true, &g->ws);
     if (s != SSSP_OK) return s;
   }
   *out = g->ws;
@@ -481,16 +667,16 @@ sssp_status workspace_get(sssp_graph* g, Workspace** out) {
 
 namespace {
 
-SolveWS ws_view(Workspace* ws, unsigned long long* d, uint32_t crit, bool has_reverse) {
+SolveWS ws_view(Workspace* ws, unsigned long long* dist, uint32_t crit, bool has_reverse) {
   SolveWS w;
   memset(&w, 0, sizeof w);
-  w.d = d ? d : ws->d;
+  w.vrec = ws->vrec;
   w.status = ws->status;
   w.q[0] = ws->q0;
   w.q[1] = ws->q1;
-  w.sp_v = ws->sp_v;
-  w.sp_base = ws->sp_base;
-  w.cur_out = (crit & (SSSP_OUT_SIMPLE | SSSP_POLICY_LEARNED)) ? ws->cur_out : nullptr;
+  w.sp = ws->sp;
+  w.dist = dist ? dist : ws->dist;
+  w.cur_out = (crit & SSSP_OUT_SIMPLE) ? ws->cur_out : nullptr;
   w.cur_in = ((crit & (SSSP_IN_SIMPLE | SSSP_POLICY_LEARNED)) && has_reverse) ? ws->cur_in : nullptr;
   w.ctl = ws->ctl;
   return w;
@@ -528,18 +714,16 @@ sssp_status solve_one(sssp_graph* g, uint32_t source, uint32_t crit, uint64_t* d
   p.source = source;
   p.crit = crit;
   p.wait_ns = wait_limit_ns();
+  p.solo_max = solo_max();
 
-  // Enough blocks to cover the vertices, at most all co-resident blocks.
-  const int max_blocks = g_blocks_per_sm * sm_count();
-  const uint64_t want = ((uint64_t)g->n + kTile - 1) / kTile;
-  const int blocks = (int)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)max_blocks));
+  const int blocks = blocks_for(g->n);
   SSSP_CUDA_TRY(cudaMemsetAsync(ws->ctl, 0, sizeof(Ctl), st));
   void* args[] = {&p};
   SSSP_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_solve_grid, dim3(blocks), dim3(kThreads), args,
                                             kSmemBytes, st));
   SSSP_CUDA_TRY(cudaMemcpyAsync(ws->ctl_host, ws->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
   if (!dist_dev)
-    SSSP_CUDA_TRY(cudaMemcpyAsync(dist_out, ws->d, g->n * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    SSSP_CUDA_TRY(cudaMemcpyAsync(dist_out, ws->dist, g->n * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
   if (sp_buf) SSSP_CUDA_TRY(cudaMemcpyAsync(settle_phase, sp_buf, g->n * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
   SSSP_CUDA_TRY(cudaStreamSynchronize(st));
   const Ctl& c = *ws->ctl_host;
@@ -570,8 +754,12 @@ sssp_status solve_one(sssp_graph* g, uint32_t source, uint32_t crit, uint64_t* d
 struct BatchPlan {
   uint32_t count = 0;
   uint32_t crit = 0;
+  uint32_t bpg = 1;                    // blocks per solve
+  uint32_t groups = 0;
   BatchItem* items = nullptr;          // device, largest graph first
   unsigned int* next = nullptr;        // device work counter
+  GroupSlot* gslots = nullptr;         // device, one per group
+  int* err = nullptr;                  // device
   std::vector<Workspace*> ws;          // one per solve
   unsigned long long* phases = nullptr;  // device [count], caller order
   bool own_phases = false;
@@ -593,25 +781,32 @@ void batch_free(sssp_batch* b) {
   for (Workspace* w : b->ws) workspace_free(w);
   cudaFree(b->items);
   cudaFree(b->next);
+  cudaFree(b->gslots);
+  cudaFree(b->err);
   if (b->own_phases) cudaFree(b->phases);
   delete b;
 }
 
-// Queue the batch on `st`: reset the work counter and every control block,
-// then one launch of resident blocks that pull solves until none is left.
+// Queue the batch on `st`: reset the work counter, group slots and every
+// control block, then one cooperative launch whose groups pull solves.
 sssp_status batch_enqueue(sssp_batch* b, cudaStream_t st) {
   SSSP_CUDA_TRY(cudaMemsetAsync(b->next, 0, sizeof(unsigned int), st));
+  SSSP_CUDA_TRY(cudaMemsetAsync(b->gslots, 0, b->groups * sizeof(GroupSlot), st));
+  SSSP_CUDA_TRY(cudaMemsetAsync(b->err, 0, sizeof(int), st));
   for (Workspace* w : b->ws) SSSP_CUDA_TRY(cudaMemsetAsync(w->ctl, 0, sizeof(Ctl), st));
-  const int blocks = (int)std::min<uint64_t>(b->count, (uint64_t)g_blocks_per_sm * sm_count());
-  k_solve_batch<<<blocks, kThreads, kSmemBytes, st>>>(b->items, b->count, b->next, b->crit, b->phases);
-  SSSP_CUDA_TRY(cudaGetLastError());
+  const int blocks = (int)(b->groups * b->bpg);
+  uint32_t solo = solo_max();
+  unsigned long long wait = wait_limit_ns();
+  void* args[] = {&b->items, &b->count, &b->next, &b->gslots, &b->bpg, &b->crit, &solo, &wait, &b->err, &b->phases};
+  SSSP_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_solve_batch, dim3(blocks), dim3(kThreads), args,
+                                            kSmemBytes, st));
   return SSSP_OK;
 }
 
 sssp_status batch_build(sssp_graph* const* graphs, const uint32_t* sources, uint32_t count, uint32_t crit,
-                        uint64_t* const* dist_out, uint64_t* phases_dev, cudaStream_t st, sssp_batch** out) {
+                        uint64_t* const* dist_out, uint64_t* phases_dev, uint32_t bpg, cudaStream_t st,
+                        sssp_batch** out) {
   if (!graphs || !sources || !dist_out || count == 0) return fail(SSSP_ERR_INVALID_ARG, "empty or NULL batch");
-  if (crit & SSSP_POLICY_LEARNED) return fail(SSSP_ERR_UNSUPPORTED, "the learned policy is not available in batches");
   for (uint32_t i = 0; i < count; ++i) {
     if (!graphs[i]) return fail(SSSP_ERR_INVALID_ARG, "graph %u is NULL", i);
     if (sources[i] >= graphs[i]->n) return fail(SSSP_ERR_INVALID_ARG, "source of solve %u out of range", i);
@@ -622,10 +817,15 @@ sssp_status batch_build(sssp_graph* const* graphs, const uint32_t* sources, uint
   }
   sssp_status s = ensure_kernel_attrs();
   if (s != SSSP_OK) return s;
+  const uint32_t resident = (uint32_t)(g_blocks_per_sm * sm_count());
+  if (bpg == 0) bpg = 1;
+  if (bpg > resident) bpg = resident;
   sssp_batch* b = new (std::nothrow) sssp_batch();
   if (!b) return fail(SSSP_ERR_OUT_OF_MEMORY, "host allocation failed");
   b->count = count;
   b->crit = crit;
+  b->bpg = bpg;
+  b->groups = std::max<uint32_t>(1, std::min<uint32_t>(count, resident / bpg));
   // Largest solves first, so the tail of the queue holds the short ones.
   std::vector<uint32_t> order(count);
   for (uint32_t i = 0; i < count; ++i) order[i] = i;
@@ -637,7 +837,7 @@ sssp_status batch_build(sssp_graph* const* graphs, const uint32_t* sources, uint
   const bool cursors = (crit & (SSSP_IN_SIMPLE | SSSP_OUT_SIMPLE)) != 0;
   for (uint32_t k = 0; k < count; ++k) {
     const uint32_t i = order[k];
-    if ((s = workspace_alloc(graphs[i]->n, cursors, &b->ws[k])) != SSSP_OK) {
+    if ((s = workspace_alloc(graphs[i]->n, cursors, false, &b->ws[k])) != SSSP_OK) {
       batch_free(b);
       return s;
     }
@@ -647,7 +847,9 @@ sssp_status batch_build(sssp_graph* const* graphs, const uint32_t* sources, uint
     h[k].out_index = i;
   }
   if (cudaMalloc(&b->items, count * sizeof(BatchItem)) != cudaSuccess ||
-      cudaMalloc(&b->next, sizeof(unsigned int)) != cudaSuccess) {
+      cudaMalloc(&b->next, sizeof(unsigned int)) != cudaSuccess ||
+      cudaMalloc(&b->gslots, b->groups * sizeof(GroupSlot)) != cudaSuccess ||
+      cudaMalloc(&b->err, sizeof(int)) != cudaSuccess) {
     batch_free(b);
     return fail(SSSP_ERR_OUT_OF_MEMORY, "device allocation failed");
   }
@@ -669,14 +871,22 @@ sssp_status batch_build(sssp_graph* const* graphs, const uint32_t* sources, uint
   return SSSP_OK;
 }
 
-// First control block that recorded an error (0 if none); reads all of them.
 sssp_status batch_status(sssp_batch* b) {
-  for (Workspace* w : b->ws) {
-    SSSP_CUDA_TRY(cudaMemcpy(w->ctl_host, w->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
-    if (w->ctl_host->err != 0) return fail((sssp_status)w->ctl_host->err, "device-side error %d in a batched solve",
-                                           w->ctl_host->err);
-  }
+  int e = 0;
+  SSSP_CUDA_TRY(cudaMemcpy(&e, b->err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (e != 0) return fail((sssp_status)e, "device-side error %d in a batched solve", e);
   return SSSP_OK;
+}
+
+// Blocks per solve for a batch: as many groups as solves while that keeps
+// every resident block busy, fewer (larger) groups for few large solves.
+uint32_t choose_bpg(sssp_graph* const* graphs, uint32_t count) {
+  const uint32_t resident = (uint32_t)(g_blocks_per_sm * sm_count());
+  uint64_t maxn = 0;
+  for (uint32_t i = 0; i < count; ++i) maxn = std::max<uint64_t>(maxn, graphs[i]->n);
+  const uint32_t bpg = std::max<uint32_t>(1, resident / std::max<uint32_t>(1, count));
+  const uint32_t useful = (uint32_t)std::max<uint64_t>(1, (maxn + kTile - 1) / kTile);
+  return std::min(bpg, useful);
 }
 
 }  // namespace
@@ -703,8 +913,14 @@ extern "C" sssp_status sssp_solve_batch(sssp_graph* const* graphs, const uint32_
   clear_error();
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const bool ph_dev = phases_out && is_device_pointer(phases_out);
+  sssp_status s = ensure_kernel_attrs();
+  if (s != SSSP_OK) return s;
+  if (!graphs || count == 0) return fail(SSSP_ERR_INVALID_ARG, "empty or NULL batch");
+  for (uint32_t i = 0; i < count; ++i)
+    if (!graphs[i]) return fail(SSSP_ERR_INVALID_ARG, "graph %u is NULL", i);
   sssp_batch* b = nullptr;
-  sssp_status s = batch_build(graphs, sources, count, criterion, dist_out, ph_dev ? phases_out : nullptr, st, &b);
+  const uint32_t bpg = batch_blocks_per_solve() ? batch_blocks_per_solve() : choose_bpg(graphs, count);
+  s = batch_build(graphs, sources, count, criterion, dist_out, ph_dev ? phases_out : nullptr, bpg, st, &b);
   if (s != SSSP_OK) return s;
   s = batch_enqueue(b, st);
   if (s == SSSP_OK && cudaStreamSynchronize(st) != cudaSuccess) s = fail(SSSP_ERR_CUDA, "batched solve failed");
@@ -723,9 +939,15 @@ extern "C" sssp_status sssp_batch_create(sssp_graph* const* graphs, const uint32
   if (!out) return fail(SSSP_ERR_INVALID_ARG, "out is NULL");
   if (phases_out && !is_device_pointer(phases_out))
     return fail(SSSP_ERR_INVALID_ARG, "phases_out of a prepared batch must be device memory");
+  sssp_status s = ensure_kernel_attrs();
+  if (s != SSSP_OK) return s;
+  if (!graphs || count == 0) return fail(SSSP_ERR_INVALID_ARG, "empty or NULL batch");
+  for (uint32_t i = 0; i < count; ++i)
+    if (!graphs[i]) return fail(SSSP_ERR_INVALID_ARG, "graph %u is NULL", i);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   sssp_batch* b = nullptr;
-  sssp_status s = batch_build(graphs, sources, count, criterion, dist_out, phases_out, st, &b);
+  const uint32_t bpg = batch_blocks_per_solve() ? batch_blocks_per_solve() : choose_bpg(graphs, count);
+  s = batch_build(graphs, sources, count, criterion, dist_out, phases_out, bpg, st, &b);
   if (s != SSSP_OK) return s;
   cudaStream_t cap = nullptr;
   if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) {

@@ -9,8 +9,10 @@ constexpr int kThreads = 512;
 constexpr int kRelaxItems = 4;
 constexpr int kTile = kThreads * kRelaxItems;
 constexpr size_t kSmemBytes = 64 * sizeof(unsigned long long)                             // reduction scratch
-                              + kTile * (sizeof(uint32_t) + 2 * sizeof(unsigned long long))  // relax tile
+                              + kTile * (2 * sizeof(uint32_t) + sizeof(unsigned long long))  // relax tile
                               + 16;
+// Phases whose fringe has at most this many vertices run on one block alone.
+constexpr uint32_t kSoloMaxDefault = 8192;
 
 struct SolveParams {
   GraphView g;
@@ -18,6 +20,8 @@ struct SolveParams {
   uint32_t source;
   uint32_t crit;
   unsigned long long wait_ns;
+  uint32_t solo_max;  // 0 disables the single-block mode
+  uint32_t pad;
 };
 
 // One whole solve per cooperative launch (all blocks co-resident), kThreads

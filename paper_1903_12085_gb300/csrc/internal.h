@@ -17,6 +17,12 @@ void clear_error();
 // Wait limit of in-kernel waits (ns).
 uint64_t wait_limit_ns();
 
+// Tuning knobs (sssp_set_tuning): largest fringe run by one block alone, and
+// blocks per solve in batches (0 = chosen from the batch).
+uint32_t solo_max();
+uint32_t batch_blocks_per_solve();
+uint32_t grid_blocks();
+
 // Returns true if p points to device (or managed) memory.
 bool is_device_pointer(const void* p);
 
@@ -60,20 +66,21 @@ namespace sssp {
 
 struct Workspace {
   uint32_t n;
-  unsigned long long* d;
+  VRec* vrec;
   uint8_t* status;
   uint32_t* q0;
   uint32_t* q1;
-  uint32_t* sp_v;
-  uint32_t* sp_base;
+  SpEnt* sp;
   uint32_t* cur_out;
   uint32_t* cur_in;
+  unsigned long long* dist;  // used when the caller's distance buffer is host memory
   Ctl* ctl;
   Ctl* ctl_host;  // pinned mirror for read-back
 };
 
 GraphView view_of(const sssp_graph* g);
 sssp_status workspace_get(sssp_graph* g, Workspace** out);
+sssp_status workspace_alloc(uint32_t n, bool want_cursors, bool want_dist, Workspace** out);
 void workspace_free(Workspace* ws);
 
 }  // namespace sssp

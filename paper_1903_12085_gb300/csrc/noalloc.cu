@@ -10,8 +10,8 @@
 // library's module is loaded onto a GPU and held until the process exits.
 //
 // The array holds, for at most kNoallocMaxVertices vertices: the vertex
-// status bytes, the two fringe queues, the relax list (vertices and degree
-// prefix), the static out/in minima, and the control block.  Every call reuses
+// status bytes, the two fringe queues, the relax list, the per-vertex
+// distance/minima records, the static out/in minima, and the control block.  Every call reuses
 // it, so the control block is cleared at the start of each call (everything
 // else is written before it is read).  Calls that overlap on the GPU race on
 // the array.  The paper has no counterpart of this entry point.
@@ -28,9 +28,9 @@ constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 constexpr size_t kOffStatus = 0;
 constexpr size_t kOffQ0 = align256(kOffStatus + kNoallocMaxVertices);
 constexpr size_t kOffQ1 = align256(kOffQ0 + 4ull * kNoallocMaxVertices);
-constexpr size_t kOffSpV = align256(kOffQ1 + 4ull * kNoallocMaxVertices);
-constexpr size_t kOffSpBase = align256(kOffSpV + 4ull * kNoallocMaxVertices);
-constexpr size_t kOffOutMin = align256(kOffSpBase + 4ull * kNoallocMaxVertices);
+constexpr size_t kOffSp = align256(kOffQ1 + 4ull * kNoallocMaxVertices);
+constexpr size_t kOffVrec = align256(kOffSp + sizeof(SpEnt) * kNoallocMaxVertices);
+constexpr size_t kOffOutMin = align256(kOffVrec + sizeof(VRec) * kNoallocMaxVertices);
 constexpr size_t kOffInMin = align256(kOffOutMin + 4ull * kNoallocMaxVertices);
 constexpr size_t kOffCtl = align256(kOffInMin + 4ull * kNoallocMaxVertices);
 constexpr size_t kScratchBytes = align256(kOffCtl + sizeof(Ctl));
@@ -153,16 +153,17 @@ extern "C" sssp_status sssp_solve_noalloc(uint32_t n, uint64_t m, const uint64_t
   p.g.edges = e2;
   p.g.out_min = out_min;
   p.g.in_min = in_min;
-  p.ws.d = reinterpret_cast<unsigned long long*>(dist_out);
+  p.ws.dist = reinterpret_cast<unsigned long long*>(dist_out);
+  p.ws.vrec = reinterpret_cast<VRec*>(base + kOffVrec);
   p.ws.status = base + kOffStatus;
   p.ws.q[0] = reinterpret_cast<uint32_t*>(base + kOffQ0);
   p.ws.q[1] = reinterpret_cast<uint32_t*>(base + kOffQ1);
-  p.ws.sp_v = reinterpret_cast<uint32_t*>(base + kOffSpV);
-  p.ws.sp_base = reinterpret_cast<uint32_t*>(base + kOffSpBase);
+  p.ws.sp = reinterpret_cast<SpEnt*>(base + kOffSp);
   p.ws.ctl = ctl;
   p.source = source;
   p.crit = criterion;
   p.wait_ns = wait_limit_ns();
+  p.solo_max = solo_max();
   const uint64_t want = ((uint64_t)n + kTile - 1) / kTile;
   const int grid = (int)(want < (uint64_t)blocks ? (want > 0 ? want : 1) : blocks);
   void* args[] = {&p};

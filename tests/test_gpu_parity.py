@@ -20,12 +20,27 @@ CRITS = [sp.IN_STATIC, sp.OUT_STATIC, sp.IN_OUT, sp.IN_SIMPLE, sp.OUT_SIMPLE, sp
 MODES = [0, sp.FRONTIER_DENSE, sp.FRONTIER_AUTO]
 
 
+# execution tunings that must not change any result: (solo_max, grid_blocks)
+TUNINGS = {"default": (8192, 0), "grid_only_3blk": (0, 3), "solo_3blk": (8, 3), "one_block": (0, 1)}
+
+
 @pytest.fixture(scope="module", autouse=True)
 def _device():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     torch.cuda.set_device(0)
     sp.set_wait_limit_ns(2_000_000_000)
+    sp.set_tuning()
+    yield
+    sp.set_tuning()
+
+
+@pytest.fixture(params=list(TUNINGS), ids=list(TUNINGS))
+def tuning(request):
+    solo, blocks = TUNINGS[request.param]
+    sp.set_tuning(solo_max_frontier=solo, grid_blocks=blocks)
+    yield request.param
+    sp.set_tuning()
 
 
 def check(g, G, s, crit, ref=None, mode=0):
@@ -60,9 +75,9 @@ def test_golden_examples_on_gpu():
 
 
 @pytest.mark.parametrize("mode", MODES, ids=["sparse", "dense", "auto"])
-def test_fuzz_tiny_graphs(mode):
+def test_fuzz_tiny_graphs(mode, tuning):
     rng = np.random.default_rng(1234 + mode % 7)
-    for case in range(150):
+    for case in range(60):
         g = P.random_tiny_graph(rng, n_max=40, w_max=int(rng.choice([0, 3, 50, 2**31])))
         s = int(rng.integers(0, g.n))
         G = sp.Graph.from_csr(g, reverse=True)
@@ -73,7 +88,7 @@ def test_fuzz_tiny_graphs(mode):
 
 
 @pytest.mark.parametrize("crit", CRITS, ids=lambda c: f"crit{c}")
-def test_workload1_full(crit):
+def test_workload1_full(crit, tuning):
     """G(16384, 131072), the full first workload, every criterion."""
     g = gg.workload(1).graphs[0]
     G = sp.Graph.from_csr(g, reverse=True)
@@ -82,7 +97,7 @@ def test_workload1_full(crit):
         check(g, G, 0, crit, ref, mode)
 
 
-def test_workload_shapes_small():
+def test_workload_shapes_small(tuning):
     """Smaller members of every workload family (several tiles, ragged tails)."""
     cases = [gg.workload(2, shrink=6), gg.workload(3, shrink=8), gg.workload(5, shrink=8)]
     for wl in cases:
