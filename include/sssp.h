@@ -205,8 +205,9 @@ void sssp_batch_destroy(sssp_batch* b);
  *   phases_out   host uint64 (may be NULL)
  * n must be in [1, SSSP_NOALLOC_MAX_VERTICES]; larger graphs are rejected with
  * SSSP_ERR_INVALID_ARG.  All scratch (status, queues, relax list, distance
- * records, static minima, control block: 49 bytes per vertex of the maximum,
- * about 25 MiB in all) is one file-scope __device__ array that every GPU loading the library
+ * records, static minima, row starts and degrees, control block: 57 bytes per
+ * vertex of the maximum, about 28.5 MiB in all) is one file-scope __device__
+ * array that every GPU loading the library
  * holds until the process exits.  The call makes no cudaMalloc/cudaFree or
  * other allocating call.  Its first call on a device looks up the array's
  * device address (cudaGetSymbolAddress) and the co-resident block count; make
@@ -218,18 +219,21 @@ sssp_status sssp_solve_noalloc(uint32_t n, uint64_t m, const uint64_t* row_offse
                                const uint32_t* edges, uint32_t source, uint32_t criterion,
                                uint64_t* dist_out, uint64_t* phases_out, void* stream);
 
-/* Execution tuning (results never depend on it).  solo_max_frontier: phases
- * whose fringe has at most this many vertices run on a single block with block
- * barriers (0 = never); batch_blocks_per_solve: blocks that cooperate on one
- * solve of a batch (0 = chosen from the batch); grid_blocks: blocks of a single
- * solve (0 = chosen from n, capped at the co-resident maximum).  Applies to
- * launches made after the call; sssp_set_tuning(NULL) restores the defaults
- * (8192, 0, 0). */
+/* Execution tuning (results never depend on it).  solo_max_frontier: a
+ * phase whose fringe has at most this many vertices (and at most 4096) runs on
+ * a single block with its queues in shared memory (0 = never); if its relax
+ * list then has more than solo_max_edges edges, the relax step is handed to
+ * all blocks of the solve;
+ * batch_blocks_per_solve: blocks that cooperate on one solve of a batch (0 =
+ * chosen from the batch); grid_blocks: blocks of a single solve (0 = chosen
+ * from n, capped at the co-resident maximum).  Applies to launches made after
+ * the call; sssp_set_tuning(NULL) restores the defaults (4096, 0, 0, 2048). */
 typedef struct {
   uint32_t solo_max_frontier;
   uint32_t batch_blocks_per_solve;
   uint32_t grid_blocks;
-  uint32_t reserved[5];
+  uint32_t solo_max_edges;
+  uint32_t reserved[4];
 } sssp_tuning;
 sssp_status sssp_set_tuning(const sssp_tuning* t);
 sssp_status sssp_get_tuning(sssp_tuning* t);

@@ -135,16 +135,20 @@ def selftest_wait(limit_ns: int) -> int:
 
 class Tuning(ctypes.Structure):
     _fields_ = [("solo_max_frontier", ctypes.c_uint32), ("batch_blocks_per_solve", ctypes.c_uint32),
-                ("grid_blocks", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 5)]
+                ("grid_blocks", ctypes.c_uint32), ("solo_max_edges", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 4)]
 
 
-def set_tuning(solo_max_frontier=None, batch_blocks_per_solve=None, grid_blocks=None):
+def set_tuning(solo_max_frontier=None, batch_blocks_per_solve=None, grid_blocks=None, solo_max_edges=None):
     """sssp_set_tuning; unspecified fields keep their current value.
     set_tuning() with no argument restores the defaults."""
-    if solo_max_frontier is None and batch_blocks_per_solve is None and grid_blocks is None:
+    if solo_max_frontier is None and batch_blocks_per_solve is None and grid_blocks is None \
+            and solo_max_edges is None:
         _check(lib().sssp_set_tuning(None))
         return
     t = get_tuning()
+    if solo_max_edges is not None:
+        t.solo_max_edges = int(solo_max_edges)
     if grid_blocks is not None:
         t.grid_blocks = int(grid_blocks)
     if solo_max_frontier is not None:

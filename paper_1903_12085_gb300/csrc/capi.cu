@@ -13,11 +13,13 @@ std::atomic<uint64_t> g_wait_ns{2000000000ull};
 std::atomic<uint32_t> g_solo_max{kSoloMaxDefault};
 std::atomic<uint32_t> g_batch_bpg{0};
 std::atomic<uint32_t> g_grid_blocks{0};
+std::atomic<uint32_t> g_solo_edges{kSoloEdgesDefault};
 }  // namespace
 
 uint32_t solo_max() { return g_solo_max.load(); }
 uint32_t batch_blocks_per_solve() { return g_batch_bpg.load(); }
 uint32_t grid_blocks() { return g_grid_blocks.load(); }
+uint32_t solo_edges() { return g_solo_edges.load(); }
 
 sssp_status fail(sssp_status st, const char* fmt, ...) {
   va_list ap;
@@ -85,11 +87,13 @@ extern "C" sssp_status sssp_set_tuning(const sssp_tuning* t) {
     sssp::g_solo_max.store(sssp::kSoloMaxDefault);
     sssp::g_batch_bpg.store(0);
     sssp::g_grid_blocks.store(0);
+    sssp::g_solo_edges.store(sssp::kSoloEdgesDefault);
     return SSSP_OK;
   }
   sssp::g_solo_max.store(t->solo_max_frontier);
   sssp::g_batch_bpg.store(t->batch_blocks_per_solve);
   sssp::g_grid_blocks.store(t->grid_blocks);
+  sssp::g_solo_edges.store(t->solo_max_edges);
   return SSSP_OK;
 }
 
@@ -99,6 +103,7 @@ extern "C" sssp_status sssp_get_tuning(sssp_tuning* t) {
   t->solo_max_frontier = sssp::g_solo_max.load();
   t->batch_blocks_per_solve = sssp::g_batch_bpg.load();
   t->grid_blocks = sssp::g_grid_blocks.load();
+  t->solo_max_edges = sssp::g_solo_edges.load();
   return SSSP_OK;
 }
 

@@ -9,12 +9,18 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
-#include "../../include/sssp.h"
+#include "sssp.h"
 
 namespace sssp {
 
 constexpr uint64_t kInf64 = ~0ull;
 constexpr uint32_t kInf32 = 0xFFFFFFFFu;
+// Tentative distances in the vertex records: an unexplored vertex holds
+// kUnexplored (larger than any distance, which is < (2^31)(2^32) < 2^63); a
+// settled vertex has kSettledBit set on top of its final distance, so one load
+// of the record tells a relaxation both d and whether the target is settled.
+constexpr uint64_t kUnexplored = 0x7FFFFFFFFFFFFFFFull;
+constexpr uint64_t kSettledBit = 0x8000000000000000ull;
 
 // Vertex status: unexplored, fringe (queued), settled (Section 2's U, F, S).
 enum : uint8_t { kU = 0, kF = 1, kS = 2 };
@@ -29,13 +35,15 @@ struct GraphView {
   const uint32_t* in_min;    // [n] static in-minimum, kInf32 if none
   const uint64_t* rrow_off;  // [n+1] in-edge CSR or nullptr
   const uint2* redges;       // [m] {source, cost}, rows sorted by (cost, source)
+  const uint2* rowdeg;       // [n] {start of out-row, out-degree} (m < 2^32)
 };
 
-// Per-vertex record gathered by the selection step: the tentative distance and
-// the minima the criteria compare it with, in one 16-byte record so that a
-// fringe entry costs one sector.  d is updated with 64-bit atomicMin.
+// Per-vertex record gathered by the selection and relax steps: the tentative
+// distance (with the settled flag, see kSettledBit) and the minima the
+// criteria compare it with, in one 16-byte load.  d is updated with 64-bit
+// atomicMin / red.min.
 //   im: in-minimum  (static, or the dynamic one when IN-SIMPLE maintains it)
-//   om: out-minimum (static, or the dynamic one when OUT-SIMPLE maintains it)
+//   om: out-minimum (static)
 struct __align__(16) VRec {
   unsigned long long d;
   uint32_t im;
@@ -80,7 +88,9 @@ struct Ctl {
   int err;                  // sssp_status recorded by a device-side failure
   unsigned int gate;        // solo mode: bumped when the leader hands back to the group
   unsigned long long heartbeat;  // solo mode: phases done by the leader (progress for waiters)
-  unsigned long long next_phase; // solo mode: phase the group resumes at (0 = solve finished)
+  unsigned long long next_phase; // solo mode: phase the group resumes at
+  unsigned int resume_relax;     // solo mode: 1 = the group resumes at the relax step of next_phase
+  unsigned int pad;
   GridBarrier bar;
 };
 
@@ -147,6 +157,10 @@ __device__ __forceinline__ VRec ldcg_vrec(const VRec* p) {
   r.im = (uint32_t)x.y;
   r.om = (uint32_t)(x.y >> 32);
   return r;
+}
+
+__device__ __forceinline__ void red_min_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("red.relaxed.gpu.global.min.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 __device__ __forceinline__ SpEnt ldcg_sp(const SpEnt* p) {
   const ulonglong2 x = __ldcg(reinterpret_cast<const ulonglong2*>(p));

@@ -162,16 +162,78 @@ __device__ __forceinline__ Mode mode_of(uint32_t crit, bool has_cur_in) {
   return m;
 }
 
+// Counters of a solve, kept in registers of the group leader (block 0,
+// thread 0) and written to the control block when the solve ends.
+struct Stats {
+  unsigned long long phases, sum_f, settled, relaxed;
+};
+
+__device__ __forceinline__ Arm arm_for(const SolveParams& p, uint32_t nF) {
+  Arm a;
+  a.in_simple = (p.crit & SSSP_IN_SIMPLE) != 0;
+  a.dense = (p.crit & SSSP_FRONTIER_DENSE) != 0 || ((p.crit & SSSP_FRONTIER_AUTO) && nF > (p.g.n >> 2));
+  return a;
+}
+
+__device__ __forceinline__ void reset_slot(PhaseSlot* s) {
+  s->min_d = s->min_out = s->a_min_d = s->a_min_out = kInf64;
+  s->relax_packed = 0;
+  s->qcount = 0;
+  s->argmin = kInf32;
+  s->settled_now = 0;
+}
+
+// Relaxation of one edge (u -> t) with d[u] = du (step C, any mode): one
+// load of t's record gives d[t] and whether t is settled (kSettledBit); a
+// settled target is skipped.  Otherwise d[t] is lowered to du + c: a target
+// still unexplored is claimed with atomicMin (its old value tells whether it is
+// new to F); any other target gets a fire-and-forget red.min.  A candidate
+// below the value read before the update contributes to the next phase's fused
+// thresholds: the final d[t] is always contributed by the relaxation that
+// wrote it, and every contribution is >= the final d[t].
+__device__ __forceinline__ void relax_edge(const SolveParams& p, const Mode& md, uint32_t t, uint32_t cost,
+                                           unsigned long long du, unsigned long long& pd, unsigned long long& po,
+                                           bool& fresh) {
+  const SolveWS& w = p.ws;
+  const VRec rt = ldcg_vrec(&w.vrec[t]);
+  if (rt.d & kSettledBit) return;
+  const unsigned long long cand = du + cost;
+  if (cand < rt.d) {
+    unsigned long long old = rt.d;
+    if (rt.d == kUnexplored) {
+      old = atomicMin(&w.vrec[t].d, cand);
+      if (old == kUnexplored) {
+        w.status[t] = kF;
+        fresh = true;
+      }
+    } else {
+      red_min_u64(&w.vrec[t].d, cand);
+    }
+    if (md.fused && cand < old) {
+      pd = cand < pd ? cand : pd;
+      if (rt.om != kInf32) {
+        const unsigned long long x = cand + rt.om;
+        po = x < po ? x : po;
+      }
+    }
+  }
+  if (md.in_maintain) {
+    const uint32_t im = in_min_dynamic(p.g, w, t, true);
+    if (im != rt.im) w.vrec[t].im = im;
+  }
+}
+
 // ---------------------------------------------------------------------------
-// One phase, run by every block of the group.  Returns false if a barrier gave up.
-__device__ bool run_phase(const SolveParams& p, const Grp& grp, const Mode& md, const Arm arm, uint64_t k,
-                          const Shared& sh) {
+// Step B of phase k (after step A for the three-step kind), by every block of
+// the group, ending with a group barrier.  Returns false if a barrier gave up.
+__device__ bool phase_select(const SolveParams& p, const Grp& grp, const Mode& md, const Arm arm, uint64_t k,
+                             const Shared& sh, Stats& st) {
   const GraphView& g = p.g;
   const SolveWS& w = p.ws;
   Ctl* ctl = w.ctl;
   const uint32_t n = g.n;
   const unsigned int tid = threadIdx.x, nthr = blockDim.x;
-  const unsigned int lane = tid & 31, warp = tid >> 5;
+  const unsigned int lane = tid & 31;
   const uint64_t gthreads = (uint64_t)grp.size * nthr;
   const uint64_t gtid = (uint64_t)grp.rank * nthr + tid;
   const bool leader = grp.rank == 0 && tid == 0;
@@ -182,19 +244,10 @@ __device__ bool run_phase(const SolveParams& p, const Grp& grp, const Mode& md, 
   PhaseSlot* S1 = &ctl->slot[(k + 1) % 3];
   const uint32_t nF = ldcg_u32(&S0->qcount);
   const bool dense = arm.dense;
-  // dynamic in-minimum used in this phase's selection
   const bool in_dyn = md.use_in && arm.in_simple && w.cur_in != nullptr;
-  unsigned long long t0 = 0;
   if (leader) {
-    t0 = globaltimer_ns();
-    PhaseSlot* S2 = &ctl->slot[(k + 2) % 3];
-    S2->min_d = S2->min_out = kInf64;
-    S2->a_min_d = S2->a_min_out = kInf64;
-    S2->relax_packed = 0;
-    S2->qcount = 0;
-    S2->argmin = kInf32;
-    S2->settled_now = 0;
-    ctl->sum_f += nF;
+    reset_slot(&ctl->slot[(k + 2) % 3]);
+    st.sum_f += nF;
   }
 
   // ---- thresholds
@@ -248,76 +301,91 @@ __device__ bool run_phase(const SolveParams& p, const Grp& grp, const Mode& md, 
 
   // ---- B: select S', mark settled, build the relax list, compact the rest of F
   unsigned long long pd = kInf64, po = kInf64;  // fused partials for phase k+1
-  {
-    const uint64_t total = dense ? n : nF;
-    uint32_t settled_here = 0;
-    for (uint64_t base = gtid & ~31ull; base < total; base += gthreads) {
-      const uint64_t i = base + lane;
-      bool valid = i < total;
-      uint32_t v = 0;
-      if (valid) {
-        v = dense ? (uint32_t)i : ldcg_u32(&Q[i]);
-        if (dense) valid = ldcg_u8(&w.status[v]) == kF;
-      }
-      bool sel = false;
-      uint32_t deg = 0, row = 0;
-      unsigned long long dv = 0;
-      if (valid) {
-        const VRec r = ldcg_vrec(&w.vrec[v]);
-        dv = r.d;
-        if (md.use_in) {
-          // record im is the dynamic minimum when maintained, else the static one
-          const uint32_t im = (in_dyn || !md.in_maintain) ? r.im : __ldg(&g.in_min[v]);
-          sel = (im == kInf32) || dv <= minD + im;
-        }
-        if (!sel && md.use_out) sel = dv <= minOut;
-        if (!sel && md.dijk) sel = (v == amin);
-        if (sel) {
-          w.status[v] = kS;
-          if (w.settle_phase) w.settle_phase[v] = (uint32_t)k;
-          const uint64_t r0 = __ldg(&g.row_off[v]);
-          row = (uint32_t)r0;
-          deg = (uint32_t)(__ldg(&g.row_off[v + 1]) - r0);
-        } else if (md.fused) {
-          pd = dv < pd ? dv : pd;
-          if (r.om != kInf32) {
-            const unsigned long long x = dv + r.om;
-            po = x < po ? x : po;
-          }
-        }
-      }
-      // relax list (settled vertices with out-edges): slots and edge range in one atomic
-      const bool rl = sel && deg > 0;
-      const unsigned int rmask = __ballot_sync(0xFFFFFFFFu, rl);
-      if (rmask) {
-        const uint32_t c = rl ? deg : 0;
-        const uint32_t incl = warp_inclusive_scan(c);
-        const uint32_t tot = __shfl_sync(0xFFFFFFFFu, incl, 31);
-        unsigned long long old = 0;
-        if (lane == 0) old = atomicAdd(&S0->relax_packed, ((unsigned long long)__popc(rmask) << 32) | tot);
-        old = __shfl_sync(0xFFFFFFFFu, old, 0);
-        if (rl) {
-          const uint32_t slot = (uint32_t)(old >> 32) + __popc(rmask & ((1u << lane) - 1u));
-          if (slot < n) {
-            const uint32_t base_e = (uint32_t)old + incl - c;
-            *reinterpret_cast<ulonglong2*>(&w.sp[slot]) =
-                make_ulonglong2(dv, (unsigned long long)row | ((unsigned long long)base_e << 32));
-          } else {
-            atomicCAS(&ctl->err, 0, (int)SSSP_ERR_INTERNAL);
-          }
-        }
-      }
-      warp_append(Qn, &S1->qcount, valid && !sel, v, n, &ctl->err);
-      settled_here += __popc(__ballot_sync(0xFFFFFFFFu, sel));
+  const uint64_t total = dense ? n : nF;
+  uint32_t settled_here = 0;
+  for (uint64_t base = gtid & ~31ull; base < total; base += gthreads) {
+    const uint64_t i = base + lane;
+    bool valid = i < total;
+    uint32_t v = 0;
+    if (valid) {
+      v = dense ? (uint32_t)i : ldcg_u32(&Q[i]);
+      if (dense) valid = ldcg_u8(&w.status[v]) == kF;
     }
-    if (lane == 0 && settled_here) atomicAdd(&S0->settled_now, settled_here);
+    bool sel = false;
+    uint32_t deg = 0, row = 0;
+    unsigned long long dv = 0;
+    if (valid) {
+      const VRec r = ldcg_vrec(&w.vrec[v]);
+      dv = r.d;
+      if (md.use_in) {
+        // record im is the dynamic minimum when maintained, else the static one
+        const uint32_t im = (in_dyn || !md.in_maintain) ? r.im : __ldg(&g.in_min[v]);
+        sel = (im == kInf32) || dv <= minD + im;
+      }
+      if (!sel && md.use_out) sel = dv <= minOut;
+      if (!sel && md.dijk) sel = (v == amin);
+      if (sel) {
+        w.status[v] = kS;
+        w.vrec[v].d = dv | kSettledBit;
+        if (w.settle_phase) w.settle_phase[v] = (uint32_t)k;
+        const uint2 rd = __ldg(&g.rowdeg[v]);
+        row = rd.x;
+        deg = rd.y;
+      } else if (md.fused) {
+        pd = dv < pd ? dv : pd;
+        if (r.om != kInf32) {
+          const unsigned long long x = dv + r.om;
+          po = x < po ? x : po;
+        }
+      }
+    }
+    // relax list (settled vertices with out-edges): slots and edge range in one atomic
+    const bool rl = sel && deg > 0;
+    const unsigned int rmask = __ballot_sync(0xFFFFFFFFu, rl);
+    if (rmask) {
+      const uint32_t c = rl ? deg : 0;
+      const uint32_t incl = warp_inclusive_scan(c);
+      const uint32_t tot = __shfl_sync(0xFFFFFFFFu, incl, 31);
+      unsigned long long old = 0;
+      if (lane == 0) old = atomicAdd(&S0->relax_packed, ((unsigned long long)__popc(rmask) << 32) | tot);
+      old = __shfl_sync(0xFFFFFFFFu, old, 0);
+      if (rl) {
+        const uint32_t slot = (uint32_t)(old >> 32) + __popc(rmask & ((1u << lane) - 1u));
+        if (slot < n) {
+          const uint32_t base_e = (uint32_t)old + incl - c;
+          *reinterpret_cast<ulonglong2*>(&w.sp[slot]) =
+              make_ulonglong2(dv, (unsigned long long)row | ((unsigned long long)base_e << 32));
+        } else {
+          atomicCAS(&ctl->err, 0, (int)SSSP_ERR_INTERNAL);
+        }
+      }
+    }
+    warp_append(Qn, &S1->qcount, valid && !sel, v, n, &ctl->err);
+    settled_here += __popc(__ballot_sync(0xFFFFFFFFu, sel));
   }
+  if (lane == 0 && settled_here) atomicAdd(&S0->settled_now, settled_here);
   if (md.fused) block_min2_to_global(pd, po, &S1->min_d, md.use_out ? &S1->min_out : nullptr, sh.red);
-  if (!grp.sync()) return false;
+  return grp.sync();
+}
 
-  // ---- C: relax every out-edge of S' (edge-balanced tiles)
-  pd = kInf64;
-  po = kInf64;
+// Step C of phase k (relax every out-edge of S', edge-balanced tiles), then
+// the end-of-phase barrier, counters and trace.  Every block of the group
+// calls it.  Returns false if a barrier gave up.
+__device__ bool phase_relax(const SolveParams& p, const Grp& grp, const Mode& md, const Arm arm, uint64_t k,
+                            const Shared& sh, Stats& st) {
+  const GraphView& g = p.g;
+  const SolveWS& w = p.ws;
+  Ctl* ctl = w.ctl;
+  const uint32_t n = g.n;
+  const unsigned int tid = threadIdx.x, nthr = blockDim.x;
+  const unsigned int lane = tid & 31, warp = tid >> 5;
+  const bool leader = grp.rank == 0 && tid == 0;
+  const int cur = (int)((k - 1) & 1);
+  uint32_t* Qn = w.q[cur ^ 1];
+  PhaseSlot* S0 = &ctl->slot[k % 3];
+  PhaseSlot* S1 = &ctl->slot[(k + 1) % 3];
+  const unsigned long long t0 = leader ? globaltimer_ns() : 0;
+  unsigned long long pd = kInf64, po = kInf64;
   const unsigned long long packed = ldcg_u64(&S0->relax_packed);
   const uint32_t nS = (uint32_t)(packed >> 32);
   const uint32_t E = (uint32_t)packed;
@@ -353,51 +421,31 @@ __device__ bool run_phase(const SolveParams& p, const Grp& grp, const Mode& md, 
         }
         const uint2 ed = __ldg(&g.edges[sh.s_row[a] + (e - sh.s_base[a])]);
         t = ed.x;
-        if (ldcg_u8(&w.status[t]) != kS) {
-          const VRec rt = ldcg_vrec(&w.vrec[t]);
-          const unsigned long long cand = sh.s_d[a] + ed.y;
-          if (cand < rt.d) {
-            const unsigned long long old = atomicMin(&w.vrec[t].d, cand);
-            if (old == kInf64) {
-              w.status[t] = kF;
-              fresh = true;
-            }
-            if (md.fused && cand < old) {
-              pd = cand < pd ? cand : pd;
-              if (rt.om != kInf32) {
-                const unsigned long long x = cand + rt.om;
-                po = x < po ? x : po;
-              }
-            }
-          }
-          if (md.in_maintain) {
-            const uint32_t im = in_min_dynamic(g, w, t, true);
-            if (im != rt.im) w.vrec[t].im = im;
-          }
-        }
+        relax_edge(p, md, t, ed.y, sh.s_d[a], pd, po, fresh);
       }
       warp_append(Qn, &S1->qcount, fresh, t, n, &ctl->err);
     }
     __syncthreads();
   }
   if (md.fused) block_min2_to_global(pd, po, &S1->min_d, md.use_out ? &S1->min_out : nullptr, sh.red);
-  if (leader) ctl->relaxed += E;
   if (!grp.sync()) return false;
   if (leader) {
     const uint32_t settled_now = ldcg_u32(&S0->settled_now);
-    ctl->settled += settled_now;
-    ctl->phases = k;
+    st.settled += settled_now;
+    st.relaxed += E;
+    st.phases = k;
     if (w.trace && k <= w.trace_cap) {
+      const bool in_dyn = md.use_in && arm.in_simple && w.cur_in != nullptr;
       sssp_phase_record r;
-      r.frontier = nF;
+      r.frontier = ldcg_u32(&S0->qcount);
       r.settled = settled_now;
-      r.min_d = minD;
-      r.min_out = md.use_out ? minOut : kInf64;
+      r.min_d = md.fused ? ldcg_u64(&S0->min_d) : ldcg_u64(&S0->a_min_d);
+      r.min_out = md.use_out ? (md.fused ? ldcg_u64(&S0->min_out) : ldcg_u64(&S0->a_min_out)) : kInf64;
       r.deg_settled = E;
       uint32_t c = p.crit & SSSP_CRITERIA_MASK;
       if (md.use_in) c = (c & ~(uint32_t)(SSSP_IN_STATIC | SSSP_IN_SIMPLE)) | (in_dyn ? SSSP_IN_SIMPLE : SSSP_IN_STATIC);
       r.criterion = c;
-      r.arm = (dense ? 1u : 0u) | (grp.size == 1 ? 2u : 0u);
+      r.arm = (arm.dense ? 1u : 0u) | (grp.size == 1 ? 2u : 0u);
       r.t_start_ns = t0;
       r.t_end_ns = globaltimer_ns();
       r.reserved = 0;
@@ -407,15 +455,324 @@ __device__ bool run_phase(const SolveParams& p, const Grp& grp, const Mode& md, 
   return true;
 }
 
-__device__ __forceinline__ Arm arm_for(const SolveParams& p, uint32_t nF) {
-  Arm a;
-  a.in_simple = (p.crit & SSSP_IN_SIMPLE) != 0;
-  a.dense = (p.crit & SSSP_FRONTIER_DENSE) != 0 || ((p.crit & SSSP_FRONTIER_AUTO) && nF > (p.g.n >> 2));
-  return a;
+__device__ __forceinline__ bool run_phase(const SolveParams& p, const Grp& grp, const Mode& md, uint64_t k,
+                                          const Shared& sh, Stats& st) {
+  const Arm arm = arm_for(p, ldcg_u32(&p.ws.ctl->slot[k % 3].qcount));
+  if (!phase_select(p, grp, md, arm, k, sh, st)) return false;
+  return phase_relax(p, grp, md, arm, k, sh, st);
 }
 
-// Initialise, run all phases (switching to solo mode while |F| is small),
-// write the distances.  Every block of the group calls it.
+// Solo episode (fused thresholds only): this block runs phases k, k+1, ...
+// alone while |F| <= min(solo_max, kSoloCap).  The two fringe queues, the
+// relax list, the counters and the thresholds live in shared memory; global
+// memory is touched only for vertex records, status bytes, edges and distance
+// updates.  Queue slots at or beyond kSoloCap go to the global queue at the
+// same index.  If a phase's relax list has more than solo_edges edges and
+// `can_handoff`, the episode stops after the selection and hands the relax step
+// to the whole group (*handoff = true).
+// Entry: global queue q[(k-1)&1] with slot[k%3].qcount entries, thresholds in
+// slot[k%3].  Exit at phase k: the same state with slot[(k+1)%3] reset (no
+// handoff), or the state after a grid selection step of phase k (handoff).
+// All threads of the block call it.
+__device__ uint64_t solo_episode(const SolveParams& p, const Mode& md, uint64_t k, unsigned char* smem, Stats& st,
+                                 bool can_handoff, bool* handoff) {
+  const GraphView& g = p.g;
+  const SolveWS& w = p.ws;
+  Ctl* ctl = w.ctl;
+  const uint32_t n = g.n;
+  const unsigned int tid = threadIdx.x, nthr = blockDim.x;
+  const unsigned int lane = tid & 31, warp = tid >> 5;
+  unsigned long long* red = reinterpret_cast<unsigned long long*>(smem);
+  uint32_t* sqa = reinterpret_cast<uint32_t*>(red + 64);
+  uint32_t* sqb = sqa + kSoloCap;
+  unsigned long long* sp_d = reinterpret_cast<unsigned long long*>(sqb + kSoloCap);
+  uint32_t* sp_row = reinterpret_cast<uint32_t*>(sp_d + kSoloCap);
+  uint32_t* sp_base = sp_row + kSoloCap;
+  // records of this phase's fringe entries, staged by queue position
+  unsigned long long* r_d = reinterpret_cast<unsigned long long*>(sp_base + kSoloCap);
+  uint32_t* r_im = reinterpret_cast<uint32_t*>(r_d + kSoloCap);
+  uint32_t* r_om = r_im + kSoloCap;
+  __shared__ unsigned int s_qn, s_settled;
+  __shared__ unsigned int s_wk[32], s_wr[32], s_we[32];  // per-warp counts, then offsets
+  __shared__ unsigned long long s_relax, s_thr_d, s_thr_o;
+  *handoff = false;
+
+  const uint32_t cap = p.solo_max < kSoloCap ? p.solo_max : kSoloCap;
+  uint32_t nF = ldcg_u32(&ctl->slot[k % 3].qcount);
+  unsigned long long minD = ldcg_u64(&ctl->slot[k % 3].min_d);
+  unsigned long long minOut = ldcg_u64(&ctl->slot[k % 3].min_out);
+  {
+    const uint32_t* gq = w.q[(k - 1) & 1];
+    uint32_t* sq = ((k - 1) & 1) ? sqb : sqa;
+    for (uint32_t i = tid; i < nF; i += nthr) sq[i] = ldcg_u32(gq + i);
+  }
+  for (;;) {
+    const int cur = (int)((k - 1) & 1);
+    const uint32_t* sq = cur ? sqb : sqa;
+    uint32_t* sqn = cur ? sqa : sqb;
+    uint32_t* gqn = w.q[cur ^ 1];
+    const Arm arm = arm_for(p, nF);
+    const bool in_dyn = md.use_in && arm.in_simple && w.cur_in != nullptr;
+    unsigned long long t0 = 0;
+    if (tid == 0) {
+      t0 = globaltimer_ns();
+      s_qn = 0;
+      s_settled = 0;
+      s_relax = 0;
+      s_thr_d = s_thr_o = kInf64;
+    }
+    // ---- B1: stage the fringe's records (all of a thread's loads in flight at once)
+    for (uint32_t i0 = tid; i0 < nF; i0 += 4 * nthr) {
+      VRec r[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const uint32_t i = i0 + j * nthr;
+        if (i < nF) r[j] = ldcg_vrec(&w.vrec[sq[i]]);
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const uint32_t i = i0 + j * nthr;
+        if (i < nF) {
+          r_d[i] = r[j].d;
+          r_im[i] = (in_dyn || !md.in_maintain) ? r[j].im : __ldg(&g.in_min[sq[i]]);
+          r_om[i] = r[j].om;
+        }
+      }
+    }
+    __syncthreads();
+    // ---- B2: select.  Pass 1 decides and issues the row loads of the settled
+    // vertices; one block scan of per-warp counts gives every warp its output
+    // offsets; pass 2 writes the kept entries and the relax list (no shared
+    // atomics on the hot counters).
+    constexpr int kIt = kSoloCap / kThreads;
+    unsigned long long pd = kInf64, po = kInf64;
+    uint32_t selm[kIt], keepm[kIt];
+    uint2 rdj[kIt];
+#pragma unroll
+    for (int j = 0; j < kIt; ++j) {
+      selm[j] = keepm[j] = 0;
+      rdj[j] = make_uint2(0, 0);
+      const uint32_t base = warp * 32 + j * nthr;
+      if (base < nF) {
+        const uint32_t i = base + lane;
+        const bool valid = i < nF;
+        bool sel = false;
+        if (valid) {
+          const unsigned long long dv = r_d[i];
+          if (md.use_in) {
+            const uint32_t im = r_im[i];
+            sel = (im == kInf32) || dv <= minD + im;
+          }
+          if (!sel && md.use_out) sel = dv <= minOut;
+          const uint32_t v = sq[i];
+          if (sel) {
+            w.status[v] = kS;
+            w.vrec[v].d = dv | kSettledBit;
+            if (w.settle_phase) w.settle_phase[v] = (uint32_t)k;
+            rdj[j] = __ldg(&g.rowdeg[v]);
+          } else {
+            pd = dv < pd ? dv : pd;
+            const uint32_t om = r_om[i];
+            if (om != kInf32) {
+              const unsigned long long x = dv + om;
+              po = x < po ? x : po;
+            }
+          }
+        }
+        selm[j] = __ballot_sync(0xFFFFFFFFu, sel);
+        keepm[j] = __ballot_sync(0xFFFFFFFFu, valid && !sel);
+      }
+    }
+    uint32_t wk = 0, wr = 0, we = 0, ws = 0;
+#pragma unroll
+    for (int j = 0; j < kIt; ++j) {
+      const bool rl = ((selm[j] >> lane) & 1u) && rdj[j].y > 0;
+      wk += __popc(keepm[j]);
+      ws += __popc(selm[j]);
+      wr += __popc(__ballot_sync(0xFFFFFFFFu, rl));
+      we += __reduce_add_sync(0xFFFFFFFFu, rl ? rdj[j].y : 0u);
+    }
+    if (lane == 0) {
+      s_wk[warp] = wk;
+      s_wr[warp] = wr;
+      s_we[warp] = we;
+      if (ws) atomicAdd(&s_settled, ws);
+    }
+    pd = warp_min_u64(pd);
+    po = warp_min_u64(po);
+    if (lane == 0) {
+      if (pd != kInf64) atomicMin(&s_thr_d, pd);
+      if (po != kInf64 && md.use_out) atomicMin(&s_thr_o, po);
+    }
+    __syncthreads();
+    if (warp == 0) {  // exclusive scan of the per-warp counts
+      const unsigned int nw = nthr >> 5;
+      const uint32_t a = lane < nw ? s_wk[lane] : 0, b = lane < nw ? s_wr[lane] : 0, c = lane < nw ? s_we[lane] : 0;
+      const uint32_t ia = warp_inclusive_scan(a), ib = warp_inclusive_scan(b), ic = warp_inclusive_scan(c);
+      if (lane < nw) {
+        s_wk[lane] = ia - a;
+        s_wr[lane] = ib - b;
+        s_we[lane] = ic - c;
+      }
+      if (lane == 31) {
+        s_qn = ia;
+        s_relax = ((unsigned long long)ib << 32) | ic;
+      }
+    }
+    __syncthreads();
+    {
+      uint32_t koff = s_wk[warp], roff = s_wr[warp], eoff = s_we[warp];
+      const unsigned int lt = (1u << lane) - 1u;
+#pragma unroll
+      for (int j = 0; j < kIt; ++j) {
+        const uint32_t base = warp * 32 + j * nthr;
+        if (base < nF) {
+          const uint32_t i = base + lane;
+          if ((keepm[j] >> lane) & 1u) {
+            const uint32_t slot = koff + __popc(keepm[j] & lt);
+            const uint32_t v = sq[i];
+            if (slot < kSoloCap) sqn[slot] = v;
+            else if (slot < n) gqn[slot] = v;
+            else atomicCAS(&ctl->err, 0, (int)SSSP_ERR_INTERNAL);
+          }
+          koff += __popc(keepm[j]);
+          const bool rl = ((selm[j] >> lane) & 1u) && rdj[j].y > 0;
+          const unsigned int rm = __ballot_sync(0xFFFFFFFFu, rl);
+          const uint32_t c = rl ? rdj[j].y : 0u;
+          const uint32_t incl = warp_inclusive_scan(c);
+          if (rl) {
+            const uint32_t slot = roff + __popc(rm & lt);  // < |S'| <= nF <= kSoloCap
+            sp_d[slot] = r_d[i];
+            sp_row[slot] = rdj[j].x;
+            sp_base[slot] = eoff + incl - c;
+          }
+          roff += __popc(rm);
+          eoff += __shfl_sync(0xFFFFFFFFu, incl, 31);
+        }
+      }
+    }
+    __syncthreads();
+    const unsigned long long packed = s_relax;
+    const uint32_t nS = (uint32_t)(packed >> 32), E = (uint32_t)packed;
+    if (can_handoff && E > p.solo_edges) {
+      // state of a grid selection step of phase k, in global memory
+      for (uint32_t j = tid; j < nS; j += nthr)
+        *reinterpret_cast<ulonglong2*>(&w.sp[j]) =
+            make_ulonglong2(sp_d[j], (unsigned long long)sp_row[j] | ((unsigned long long)sp_base[j] << 32));
+      const uint32_t kept = s_qn;
+      const uint32_t nk = kept < kSoloCap ? kept : kSoloCap;
+      for (uint32_t j = tid; j < nk; j += nthr) gqn[j] = sqn[j];
+      if (tid == 0) {
+        st.sum_f += nF;
+        PhaseSlot* S0 = &ctl->slot[k % 3];
+        PhaseSlot* S1 = &ctl->slot[(k + 1) % 3];
+        reset_slot(S0);
+        reset_slot(S1);
+        reset_slot(&ctl->slot[(k + 2) % 3]);
+        S0->qcount = nF;
+        S0->min_d = minD;
+        S0->min_out = minOut;
+        S0->relax_packed = packed;
+        S0->settled_now = s_settled;
+        S1->qcount = kept;
+        S1->min_d = s_thr_d;
+        S1->min_out = s_thr_o;
+      }
+      __threadfence();
+      __syncthreads();
+      *handoff = true;
+      return k;
+    }
+    // ---- C: relax
+    pd = kInf64;
+    po = kInf64;
+    for (uint32_t eb = warp * 32; eb < E; eb += nthr) {
+      const uint32_t e = eb + lane;
+      bool fresh = false;
+      uint32_t t = 0;
+      if (e < E) {
+        uint32_t a = 0, b = nS;
+        while (b - a > 1) {
+          const uint32_t mid = (a + b) >> 1;
+          if (sp_base[mid] <= e) a = mid; else b = mid;
+        }
+        const uint2 ed = __ldg(&g.edges[sp_row[a] + (e - sp_base[a])]);
+        t = ed.x;
+        relax_edge(p, md, t, ed.y, sp_d[a], pd, po, fresh);
+      }
+      const unsigned int fmask = __ballot_sync(0xFFFFFFFFu, fresh);
+      if (fmask) {
+        unsigned int b0 = 0;
+        if (lane == 0) b0 = atomicAdd(&s_qn, (unsigned int)__popc(fmask));
+        b0 = __shfl_sync(0xFFFFFFFFu, b0, 0);
+        if (fresh) {
+          const uint32_t slot = b0 + __popc(fmask & ((1u << lane) - 1u));
+          if (slot < kSoloCap) sqn[slot] = t;
+          else if (slot < n) gqn[slot] = t;
+          else atomicCAS(&ctl->err, 0, (int)SSSP_ERR_INTERNAL);
+        }
+      }
+    }
+    pd = warp_min_u64(pd);
+    po = warp_min_u64(po);
+    if (lane == 0) {
+      if (pd != kInf64) atomicMin(&s_thr_d, pd);
+      if (po != kInf64 && md.use_out) atomicMin(&s_thr_o, po);
+    }
+    __syncthreads();
+    const uint32_t nFn = s_qn;
+    if (tid == 0) {
+      st.phases = k;
+      st.sum_f += nF;
+      st.settled += s_settled;
+      st.relaxed += E;
+      ctl->heartbeat = k;
+      if (w.trace && k <= w.trace_cap) {
+        sssp_phase_record r;
+        r.frontier = nF;
+        r.settled = s_settled;
+        r.min_d = minD;
+        r.min_out = md.use_out ? minOut : kInf64;
+        r.deg_settled = E;
+        uint32_t c = p.crit & SSSP_CRITERIA_MASK;
+        if (md.use_in) c = (c & ~(uint32_t)(SSSP_IN_STATIC | SSSP_IN_SIMPLE)) | (in_dyn ? SSSP_IN_SIMPLE : SSSP_IN_STATIC);
+        r.criterion = c;
+        r.arm = 2u;
+        r.t_start_ns = t0;
+        r.t_end_ns = globaltimer_ns();
+        r.reserved = 0;
+        w.trace[k - 1] = r;
+      }
+    }
+    minD = s_thr_d;
+    minOut = s_thr_o;
+    nF = nFn;
+    ++k;
+    __syncthreads();  // shared counters are read before the next phase resets them
+    if (nF == 0 || nF > cap) break;
+  }
+  // hand the state back in global memory for phase k
+  {
+    const uint32_t* sq = ((k - 1) & 1) ? sqb : sqa;
+    uint32_t* gq = w.q[(k - 1) & 1];
+    const uint32_t ns = nF < kSoloCap ? nF : kSoloCap;
+    for (uint32_t i = tid; i < ns; i += nthr) gq[i] = sq[i];
+  }
+  if (tid == 0) {
+    PhaseSlot* S0 = &ctl->slot[k % 3];
+    reset_slot(S0);
+    reset_slot(&ctl->slot[(k + 1) % 3]);
+    S0->qcount = nF;
+    S0->min_d = minD;
+    S0->min_out = minOut;
+  }
+  __threadfence();
+  __syncthreads();
+  return k;
+}
+
+// Initialise, run all phases (switching to solo mode while the fringe is
+// small), write the distances.  Every block of the group calls it.
 __device__ void solve_body(const SolveParams& p, const Grp& grp, unsigned char* smem) {
   const GraphView& g = p.g;
   const SolveWS& w = p.ws;
@@ -427,28 +784,30 @@ __device__ void solve_body(const SolveParams& p, const Grp& grp, unsigned char* 
   const bool leader = grp.rank == 0 && tid == 0;
   const Shared sh = carve(smem);
   const Mode md = mode_of(p.crit, w.cur_in != nullptr);
+  Stats st{0, 0, 0, 0};
 
   for (uint64_t v = gtid; v < n; v += gthreads) {
     const uint32_t im = __ldg(&g.in_min[v]), om = __ldg(&g.out_min[v]);
     *reinterpret_cast<ulonglong2*>(&w.vrec[v]) =
-        make_ulonglong2(kInf64, (unsigned long long)im | ((unsigned long long)om << 32));
+        make_ulonglong2(kUnexplored, (unsigned long long)im | ((unsigned long long)om << 32));
     w.status[v] = kU;
     if (w.cur_out) w.cur_out[v] = (uint32_t)g.row_off[v];
     if (w.cur_in) w.cur_in[v] = (uint32_t)g.rrow_off[v];
     if (w.settle_phase) w.settle_phase[v] = 0;
   }
+  // Small graphs: pull the edge array into L2 now (coalesced, all blocks)
+  // instead of paying an HBM round trip on the first touch of every edge.
+  if ((uint64_t)g.m * sizeof(uint2) + (uint64_t)n * (sizeof(VRec) + sizeof(uint2)) <= kL2PrefetchBytes) {
+    const char* base = reinterpret_cast<const char*>(g.edges);
+    const uint64_t lines = ((uint64_t)g.m * sizeof(uint2) + 127) / 128;
+    for (uint64_t l = gtid; l < lines; l += gthreads)
+      asm volatile("prefetch.global.L2::evict_last [%0];" ::"l"(base + l * 128));
+  }
   if (leader) {
-    for (int j = 0; j < 3; ++j) {
-      PhaseSlot* s = &ctl->slot[j];
-      s->min_d = s->min_out = s->a_min_d = s->a_min_out = kInf64;
-      s->relax_packed = 0;
-      s->qcount = 0;
-      s->argmin = kInf32;
-      s->settled_now = 0;
-    }
-    ctl->phases = ctl->sum_f = ctl->settled = ctl->relaxed = 0;
+    for (int j = 0; j < 3; ++j) reset_slot(&ctl->slot[j]);
     ctl->heartbeat = 0;
     ctl->next_phase = 0;
+    ctl->resume_relax = 0;
   }
   if (!grp.sync()) return;
   if (leader) {
@@ -463,50 +822,76 @@ __device__ void solve_body(const SolveParams& p, const Grp& grp, unsigned char* 
   }
   if (!grp.sync()) return;
 
+  const bool dense_forced = (p.crit & SSSP_FRONTIER_DENSE) != 0;
+  const uint32_t solo_cap = p.solo_max < kSoloCap ? p.solo_max : kSoloCap;
   unsigned int episodes = 0;
   uint64_t k = 1;
   for (;;) {
     uint32_t nF = ldcg_u32(&ctl->slot[k % 3].qcount);
     if (nF == 0) break;
-    if (grp.size > 1 && nF <= p.solo_max) {
+    const bool fast_solo = md.fused && !dense_forced && nF <= solo_cap;
+    const bool generic_solo = !md.fused && grp.size > 1 && nF <= p.solo_max;
+    if (fast_solo || generic_solo) {
       __shared__ unsigned long long s_next;
-      __shared__ int s_ok;
+      __shared__ int s_ok, s_resume;
+      bool resume_relax = false;
       if (grp.rank == 0) {
-        // block 0 alone, block barriers, until |F| grows or the solve ends
-        const Grp solo{grp.bar, grp.err, grp.limit, 0, 1};
-        bool ok = true;
-        while (nF != 0 && nF <= p.solo_max) {
-          if (!run_phase(p, solo, md, arm_for(p, nF), k, sh)) { ok = false; break; }
-          ++k;
-          if (tid == 0) ctl->heartbeat = k;
-          nF = ldcg_u32(&ctl->slot[k % 3].qcount);
+        if (fast_solo) {
+          k = solo_episode(p, md, k, smem, st, grp.size > 1, &resume_relax);
+        } else {
+          // three-step kind: the generic phase on this block alone
+          const Grp solo{grp.bar, grp.err, grp.limit, 0, 1};
+          while (nF != 0 && nF <= p.solo_max) {
+            run_phase(p, solo, md, k, sh, st);
+            ++k;
+            if (tid == 0) ctl->heartbeat = k;
+            nF = ldcg_u32(&ctl->slot[k % 3].qcount);
+          }
         }
-        __syncthreads();
-        if (tid == 0) {
-          ctl->next_phase = k;
-          __threadfence();
-          red_release_gpu_add(&ctl->gate, 1u);
+        if (grp.size > 1) {
+          __syncthreads();
+          if (tid == 0) {
+            ctl->next_phase = k;
+            ctl->resume_relax = resume_relax ? 1u : 0u;
+            __threadfence();
+            red_release_gpu_add(&ctl->gate, 1u);
+          }
+          __syncthreads();
         }
-        __syncthreads();
-        if (!ok) return;
       } else {
         if (tid == 0) {
           s_ok = bounded_wait_change(&ctl->gate, episodes, grp.limit, grp.err, &ctl->heartbeat) ? 1 : 0;
           s_next = ld_relaxed_gpu_u64(&ctl->next_phase);
+          s_resume = (int)ldcg_u32(&ctl->resume_relax);
         }
         __syncthreads();
         if (!s_ok) return;
         k = s_next;
+        resume_relax = s_resume != 0;
         __syncthreads();
       }
       ++episodes;
+      if (resume_relax) {
+        const Arm arm = arm_for(p, ldcg_u32(&ctl->slot[k % 3].qcount));
+        if (!phase_relax(p, grp, md, arm, k, sh, st)) return;
+        ++k;
+      }
       continue;
     }
-    if (!run_phase(p, grp, md, arm_for(p, nF), k, sh)) return;
+    if (!run_phase(p, grp, md, k, sh, st)) return;
     ++k;
   }
+  if (leader) {
+    ctl->phases = st.phases;
+    ctl->sum_f = st.sum_f;
+    ctl->settled = st.settled;
+    ctl->relaxed = st.relaxed;
+  }
   if (!grp.sync()) return;
-  for (uint64_t v = gtid; v < n; v += gthreads) w.dist[v] = ldcg_u64(&w.vrec[v].d);
+  for (uint64_t v = gtid; v < n; v += gthreads) {
+    const unsigned long long d = ldcg_u64(&w.vrec[v].d) & ~kSettledBit;
+    w.dist[v] = d == kUnexplored ? kInf64 : d;
+  }
 }
 
 __global__ void __launch_bounds__(kThreads) k_solve_grid(SolveParams p) {
@@ -533,7 +918,7 @@ struct GroupSlot {
 
 __global__ void __launch_bounds__(kThreads) k_solve_batch(const BatchItem* items, uint32_t count,
                                                            unsigned int* next, GroupSlot* groups, uint32_t bpg,
-                                                           uint32_t crit, uint32_t solo_max,
+                                                           uint32_t crit, uint32_t solo_max, uint32_t solo_edges,
                                                            unsigned long long wait_ns, int* err,
                                                            unsigned long long* phases_out) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -555,8 +940,8 @@ __global__ void __launch_bounds__(kThreads) k_solve_batch(const BatchItem* items
     p.source = items[it].source;
     p.crit = crit;
     p.wait_ns = wait_ns;
-    p.solo_max = bpg > 1 ? solo_max : 0;
-    p.pad = 0;
+    p.solo_max = solo_max;
+    p.solo_edges = solo_edges;
     solve_body(p, grp, smem);
     if (*(volatile int*)err != 0) return;
     if (rank == 0 && threadIdx.x == 0) {
@@ -715,6 +1100,7 @@ sssp_status solve_one(sssp_graph* g, uint32_t source, uint32_t crit, uint64_t* d
   p.crit = crit;
   p.wait_ns = wait_limit_ns();
   p.solo_max = solo_max();
+  p.solo_edges = solo_edges();
 
   const int blocks = blocks_for(g->n);
   SSSP_CUDA_TRY(cudaMemsetAsync(ws->ctl, 0, sizeof(Ctl), st));
@@ -795,9 +1181,9 @@ sssp_status batch_enqueue(sssp_batch* b, cudaStream_t st) {
   SSSP_CUDA_TRY(cudaMemsetAsync(b->err, 0, sizeof(int), st));
   for (Workspace* w : b->ws) SSSP_CUDA_TRY(cudaMemsetAsync(w->ctl, 0, sizeof(Ctl), st));
   const int blocks = (int)(b->groups * b->bpg);
-  uint32_t solo = solo_max();
+  uint32_t solo = solo_max(), solo_e = solo_edges();
   unsigned long long wait = wait_limit_ns();
-  void* args[] = {&b->items, &b->count, &b->next, &b->gslots, &b->bpg, &b->crit, &solo, &wait, &b->err, &b->phases};
+  void* args[] = {&b->items, &b->count, &b->next, &b->gslots, &b->bpg, &b->crit, &solo, &solo_e, &wait, &b->err, &b->phases};
   SSSP_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_solve_batch, dim3(blocks), dim3(kThreads), args,
                                             kSmemBytes, st));
   return SSSP_OK;

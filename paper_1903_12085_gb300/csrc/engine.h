@@ -8,11 +8,23 @@ namespace sssp {
 constexpr int kThreads = 512;
 constexpr int kRelaxItems = 4;
 constexpr int kTile = kThreads * kRelaxItems;
-constexpr size_t kSmemBytes = 64 * sizeof(unsigned long long)                             // reduction scratch
-                              + kTile * (2 * sizeof(uint32_t) + sizeof(unsigned long long))  // relax tile
-                              + 16;
-// Phases whose fringe has at most this many vertices run on one block alone.
-constexpr uint32_t kSoloMaxDefault = 8192;
+// Solo mode (one block runs whole phases with its queues in shared memory):
+// fringe and relax list hold at most kSoloCap entries.
+constexpr uint32_t kSoloCap = 4096;
+constexpr uint32_t kSoloMaxDefault = kSoloCap;     // fringe size limit
+constexpr uint32_t kSoloEdgesDefault = 2048;       // relax edges above which a solo phase hands off
+constexpr size_t kGridSmem = 64 * sizeof(unsigned long long)                               // reduction scratch
+                             + kTile * (2 * sizeof(uint32_t) + sizeof(unsigned long long))  // relax tile
+                             + 16;
+constexpr size_t kSoloSmem = 64 * sizeof(unsigned long long)                       // reduction scratch
+                             + 2 * kSoloCap * sizeof(uint32_t)                     // two queues
+                             + kSoloCap * (2 * sizeof(uint32_t) + sizeof(unsigned long long))  // relax list
+                             + kSoloCap * (sizeof(unsigned long long) + 2 * sizeof(uint32_t))  // staged records
+                             + 16;
+// Graphs whose edges and vertex records take at most this many bytes are
+// prefetched into L2 when a solve starts (L2 holds 126 MiB).
+constexpr uint64_t kL2PrefetchBytes = 96ull << 20;
+constexpr size_t kSmemBytes = kGridSmem > kSoloSmem ? kGridSmem : kSoloSmem;
 
 struct SolveParams {
   GraphView g;
@@ -20,8 +32,8 @@ struct SolveParams {
   uint32_t source;
   uint32_t crit;
   unsigned long long wait_ns;
-  uint32_t solo_max;  // 0 disables the single-block mode
-  uint32_t pad;
+  uint32_t solo_max;    // largest fringe run by one block alone (0 = never)
+  uint32_t solo_edges;  // largest total fringe out-degree run by one block alone
 };
 
 // One whole solve per cooperative launch (all blocks co-resident), kThreads

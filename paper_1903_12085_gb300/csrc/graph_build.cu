@@ -210,9 +210,11 @@ __global__ void k_fill_u32(uint32_t* p, uint64_t n, uint32_t v) {
 }
 
 __global__ void k_out_min(const uint64_t* __restrict__ ro, const uint2* __restrict__ edges, uint32_t n,
-                          uint32_t* __restrict__ out_min) {
-  for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x)
+                          uint32_t* __restrict__ out_min, uint2* __restrict__ rowdeg) {
+  for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
     out_min[u] = ro[u + 1] > ro[u] ? edges[ro[u]].y : kInf32;
+    rowdeg[u] = make_uint2((uint32_t)ro[u], (uint32_t)(ro[u + 1] - ro[u]));
+  }
 }
 
 __global__ void k_in_min(const uint2* __restrict__ edges, uint64_t m, uint32_t* __restrict__ in_min) {
@@ -386,6 +388,7 @@ void free_graph(sssp_graph* g) {
   cudaFree(g->edges);
   cudaFree(g->out_min);
   cudaFree(g->in_min);
+  cudaFree(g->rowdeg);
   cudaFree(g->rrow_off);
   cudaFree(g->redges);
   delete g;
@@ -400,6 +403,7 @@ sssp_status build(sssp_graph* g, const uint64_t* ro_in, const uint32_t* col_in, 
   SSSP_CUDA_TRY(cudaMalloc(&g->edges, std::max<uint64_t>(m, 1) * sizeof(uint2)));
   SSSP_CUDA_TRY(cudaMalloc(&g->out_min, n * sizeof(uint32_t)));
   SSSP_CUDA_TRY(cudaMalloc(&g->in_min, n * sizeof(uint32_t)));
+  SSSP_CUDA_TRY(cudaMalloc(&g->rowdeg, n * sizeof(uint2)));
   SSSP_CUDA_TRY(cudaMemcpyAsync(g->row_off, ro_in, (n + 1ull) * sizeof(uint64_t), kind, st));
   if (m > 0) {
     uint32_t* tmp = nullptr;
@@ -433,7 +437,7 @@ sssp_status build(sssp_graph* g, const uint64_t* ro_in, const uint32_t* col_in, 
   }
   sssp_status s = sort_rows(g->row_off, n, m, reinterpret_cast<unsigned long long*>(g->edges), st);
   if (s != SSSP_OK) return s;
-  k_out_min<<<grid_for(n, 256), 256, 0, st>>>(g->row_off, g->edges, n, g->out_min);
+  k_out_min<<<grid_for(n, 256), 256, 0, st>>>(g->row_off, g->edges, n, g->out_min, g->rowdeg);
   k_fill_u32<<<grid_for(n, 256), 256, 0, st>>>(g->in_min, n, kInf32);
   if (m > 0) k_in_min<<<grid_for(m, 256), 256, 0, st>>>(g->edges, m, g->in_min);
   SSSP_CUDA_TRY(cudaGetLastError());
@@ -469,6 +473,7 @@ GraphView view_of(const sssp_graph* g) {
   v.edges = g->edges;
   v.out_min = g->out_min;
   v.in_min = g->in_min;
+  v.rowdeg = g->rowdeg;
   v.rrow_off = g->rrow_off;
   v.redges = g->redges;
   return v;

@@ -5,7 +5,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
-#include "../../include/sssp.h"
+#include "sssp.h"
 #include "common.cuh"
 
 namespace sssp {
@@ -22,6 +22,7 @@ uint64_t wait_limit_ns();
 uint32_t solo_max();
 uint32_t batch_blocks_per_solve();
 uint32_t grid_blocks();
+uint32_t solo_edges();
 
 // Returns true if p points to device (or managed) memory.
 bool is_device_pointer(const void* p);
@@ -56,6 +57,7 @@ struct sssp_graph {
   uint2* edges;        // device [m]
   uint32_t* out_min;   // device [n]
   uint32_t* in_min;    // device [n]
+  uint2* rowdeg;       // device [n] {row start, out-degree}
   uint64_t* rrow_off;  // device [n+1] or nullptr
   uint2* redges;       // device [m] or nullptr
   // Lazily allocated solve workspace (shared by solves on this handle).

@@ -11,7 +11,8 @@
 //
 // The array holds, for at most kNoallocMaxVertices vertices: the vertex
 // status bytes, the two fringe queues, the relax list, the per-vertex
-// distance/minima records, the static out/in minima, and the control block.  Every call reuses
+// distance/minima records, the static out/in minima, the out-row starts and
+// degrees, and the control block.  Every call reuses
 // it, so the control block is cleared at the start of each call (everything
 // else is written before it is read).  Calls that overlap on the GPU race on
 // the array.  The paper has no counterpart of this entry point.
@@ -32,7 +33,8 @@ constexpr size_t kOffSp = align256(kOffQ1 + 4ull * kNoallocMaxVertices);
 constexpr size_t kOffVrec = align256(kOffSp + sizeof(SpEnt) * kNoallocMaxVertices);
 constexpr size_t kOffOutMin = align256(kOffVrec + sizeof(VRec) * kNoallocMaxVertices);
 constexpr size_t kOffInMin = align256(kOffOutMin + 4ull * kNoallocMaxVertices);
-constexpr size_t kOffCtl = align256(kOffInMin + 4ull * kNoallocMaxVertices);
+constexpr size_t kOffRowDeg = align256(kOffInMin + 4ull * kNoallocMaxVertices);
+constexpr size_t kOffCtl = align256(kOffRowDeg + 8ull * kNoallocMaxVertices);
 constexpr size_t kScratchBytes = align256(kOffCtl + sizeof(Ctl));
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
@@ -57,6 +59,7 @@ sssp_status setup_for_current_device(DeviceSetup** out) {
   if (!s.ready) {
     void* p = nullptr;
     SSSP_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    SSSP_CUDA_TRY(cudaFuncSetAttribute(k_solve_grid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes));
     int per_sm = 0;
     SSSP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_grid, kThreads, kSmemBytes));
     if (per_sm < 1) return fail(SSSP_ERR_CUDA, "solve kernel cannot be resident");
@@ -78,7 +81,8 @@ __global__ void k_noalloc_minima_init(uint32_t n, uint32_t* out_min, uint32_t* i
 // Static minima over unsorted rows, plus validation of the caller's CSR
 // (bad[0] set on an out-of-range target, a reserved cost or bad offsets).
 __global__ void k_noalloc_minima(uint32_t n, uint64_t m, const uint64_t* __restrict__ ro,
-                                 const uint2* __restrict__ edges, uint32_t* out_min, uint32_t* in_min, int* bad) {
+                                 const uint2* __restrict__ edges, uint32_t* out_min, uint32_t* in_min,
+                                 uint2* rowdeg, int* bad) {
   const uint32_t lane = threadIdx.x & 31;
   const uint64_t warp0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
   const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -99,7 +103,10 @@ __global__ void k_noalloc_minima(uint32_t n, uint64_t m, const uint64_t* __restr
       red_min_u32(&in_min[ed.x], ed.y);
     }
     best = __reduce_min_sync(0xFFFFFFFFu, best);
-    if (lane == 0) out_min[u] = best;
+    if (lane == 0) {
+      out_min[u] = best;
+      rowdeg[u] = make_uint2((uint32_t)b, (uint32_t)(e - b));
+    }
   }
 }
 
@@ -131,13 +138,14 @@ extern "C" sssp_status sssp_solve_noalloc(uint32_t n, uint64_t m, const uint64_t
   uint32_t* out_min = reinterpret_cast<uint32_t*>(base + kOffOutMin);
   uint32_t* in_min = reinterpret_cast<uint32_t*>(base + kOffInMin);
   Ctl* ctl = reinterpret_cast<Ctl*>(base + kOffCtl);
+  uint2* rowdeg = reinterpret_cast<uint2*>(base + kOffRowDeg);
   const uint2* e2 = reinterpret_cast<const uint2*>(edges);
 
   // Clear the control block (barrier counters, error word), then the minima.
   SSSP_CUDA_TRY(cudaMemsetAsync(ctl, 0, sizeof(Ctl), st));
   const int blocks = dev->max_blocks;
   k_noalloc_minima_init<<<blocks, 256, 0, st>>>(n, out_min, in_min);
-  k_noalloc_minima<<<blocks, 256, 0, st>>>(n, m, row_offsets, e2, out_min, in_min, &ctl->err);
+  k_noalloc_minima<<<blocks, 256, 0, st>>>(n, m, row_offsets, e2, out_min, in_min, rowdeg, &ctl->err);
   SSSP_CUDA_TRY(cudaGetLastError());
   int bad = 0;
   SSSP_CUDA_TRY(cudaMemcpyAsync(&bad, &ctl->err, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -153,6 +161,7 @@ extern "C" sssp_status sssp_solve_noalloc(uint32_t n, uint64_t m, const uint64_t
   p.g.edges = e2;
   p.g.out_min = out_min;
   p.g.in_min = in_min;
+  p.g.rowdeg = rowdeg;
   p.ws.dist = reinterpret_cast<unsigned long long*>(dist_out);
   p.ws.vrec = reinterpret_cast<VRec*>(base + kOffVrec);
   p.ws.status = base + kOffStatus;
@@ -164,6 +173,7 @@ extern "C" sssp_status sssp_solve_noalloc(uint32_t n, uint64_t m, const uint64_t
   p.crit = criterion;
   p.wait_ns = wait_limit_ns();
   p.solo_max = solo_max();
+  p.solo_edges = solo_edges();
   const uint64_t want = ((uint64_t)n + kTile - 1) / kTile;
   const int grid = (int)(want < (uint64_t)blocks ? (want > 0 ? want : 1) : blocks);
   void* args[] = {&p};

@@ -20,8 +20,9 @@ CRITS = [sp.IN_STATIC, sp.OUT_STATIC, sp.IN_OUT, sp.IN_SIMPLE, sp.OUT_SIMPLE, sp
 MODES = [0, sp.FRONTIER_DENSE, sp.FRONTIER_AUTO]
 
 
-# execution tunings that must not change any result: (solo_max, grid_blocks)
-TUNINGS = {"default": (8192, 0), "grid_only_3blk": (0, 3), "solo_3blk": (8, 3), "one_block": (0, 1)}
+# execution tunings that must not change any result: (solo_max, grid_blocks, solo_edges)
+TUNINGS = {"default": (4096, 0, 2048), "grid_only_3blk": (0, 3, 0), "solo_3blk": (8, 3, 4096),
+           "solo_edges_3blk": (4096, 3, 24), "one_block": (0, 1, 0), "one_block_solo": (4096, 1, 1 << 30)}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -37,8 +38,8 @@ def _device():
 
 @pytest.fixture(params=list(TUNINGS), ids=list(TUNINGS))
 def tuning(request):
-    solo, blocks = TUNINGS[request.param]
-    sp.set_tuning(solo_max_frontier=solo, grid_blocks=blocks)
+    solo, blocks, edges = TUNINGS[request.param]
+    sp.set_tuning(solo_max_frontier=solo, grid_blocks=blocks, solo_max_edges=edges)
     yield request.param
     sp.set_tuning()
 
@@ -77,7 +78,7 @@ def test_golden_examples_on_gpu():
 @pytest.mark.parametrize("mode", MODES, ids=["sparse", "dense", "auto"])
 def test_fuzz_tiny_graphs(mode, tuning):
     rng = np.random.default_rng(1234 + mode % 7)
-    for case in range(60):
+    for case in range(40):
         g = P.random_tiny_graph(rng, n_max=40, w_max=int(rng.choice([0, 3, 50, 2**31])))
         s = int(rng.integers(0, g.n))
         G = sp.Graph.from_csr(g, reverse=True)
