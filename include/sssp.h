@@ -68,7 +68,7 @@ enum {
   SSSP_DIJK = 1u << 6,
   SSSP_CRITERIA_MASK = 0xFFFFu,
   /* Execution options (do not change results, only speed). */
-  SSSP_POLICY_LEARNED = 1u << 16,  /* per-phase arm chosen by the loaded policy network */
+  SSSP_POLICY_LEARNED = 1u << 16,  /* per-phase arm chosen by the loaded policy network (below) */
   SSSP_FRONTIER_DENSE = 1u << 17,  /* scan the vertex-status array instead of the queue */
   SSSP_FRONTIER_AUTO = 1u << 18    /* dense when |F| > n/8, else sparse */
 };
@@ -186,6 +186,51 @@ sssp_status sssp_batch_create(sssp_graph* const* graphs, const uint32_t* sources
                               void* stream, sssp_batch** out);
 sssp_status sssp_batch_launch(sssp_batch* b, void* stream);
 void sssp_batch_destroy(sssp_batch* b);
+
+/* ---- per-phase policy network ------------------------------------------
+ * With SSSP_POLICY_LEARNED (criterion bits must be IN_STATIC | OUT_STATIC, the
+ * fallback arm) every phase picks one of four arms:
+ *   0: IN-STATIC | OUT-STATIC, sparse queue   1: the same, dense scan
+ *   2: IN-SIMPLE | OUT-STATIC, sparse queue   3: the same, dense scan
+ * with a small MLP over 8 phase-start features (IN-SIMPLE arms need a graph
+ * built with SSSP_GRAPH_REVERSE).  Every arm is sound and complete (Section 3),
+ * so distances never depend on the policy; phase counts do, and
+ * sssp_solve_trace reports each phase's criterion and arm
+ * (arm field: bit 0 dense, bit 1 single-block, bit 7 policy, bits 8..15 index).
+ * Network: W1[8][32] b1[32] W2[32][32] b2[32] W3[32][4] b3[4] (float32,
+ * input index first, ReLU after both hidden layers); outputs are predicted
+ * log2(phase time / settled vertices) per arm and the smallest one wins.
+ * Features (sssp_policy_features computes them on the host):
+ *   log2(1+|F|)/24, |F|/n, log2(1+E')/24, log2(1+S')/24, log2(1+k)/16,
+ *   log2(n)/32, (m/n)/32, S'/(1+F')
+ * with E', S', F' the relaxed edges, settled vertices and fringe size of the
+ * previous phase and k the phase index. */
+#define SSSP_POLICY_FEATURES 8
+#define SSSP_POLICY_ARMS 4
+#define SSSP_POLICY_WEIGHTS 1476
+
+/* Load the network (host or device float32[SSSP_POLICY_WEIGHTS]) for the
+ * current device; it is used by solves made after the call.  The library
+ * keeps its own device copy until sssp_policy_clear. */
+sssp_status sssp_policy_load(const float* weights, size_t count);
+sssp_status sssp_policy_clear(void);
+
+/* The 8 features of a phase (host function, same formula as the device). */
+sssp_status sssp_policy_features(uint64_t frontier, uint64_t n, uint64_t m, uint64_t phase,
+                                 uint64_t edges_prev, uint64_t settled_prev, uint64_t frontier_prev,
+                                 float* out8);
+
+/* FP32 training kernels (all pointers device memory, stream-ordered):
+ *   sssp_mlp_forward   y[b][0..3] = network(x[b][0..7]) for b < batch
+ *   sssp_mlp_backward  grad[SSSP_POLICY_WEIGHTS] = d loss / d w and *loss =
+ *                      (1/B) sum_b (y_b[arm[b]] - target[b])^2 (loss may be
+ *                      NULL); fixed summation order (deterministic)
+ *   sssp_mlp_adam      one Adam step (bias-corrected with `step` >= 1) */
+sssp_status sssp_mlp_forward(const float* w, const float* x, uint32_t batch, float* y, void* stream);
+sssp_status sssp_mlp_backward(const float* w, const float* x, const float* target, const uint32_t* arm,
+                              uint32_t batch, float* grad, float* loss, void* stream);
+sssp_status sssp_mlp_adam(float* w, const float* grad, float* m1, float* m2, uint32_t count, float lr,
+                          float beta1, float beta2, float eps, uint32_t step, void* stream);
 
 /* Largest n accepted by sssp_solve_noalloc. */
 #define SSSP_NOALLOC_MAX_VERTICES (1u << 19)

@@ -81,6 +81,13 @@ def lib():
             "sssp_solve_noalloc": [u32, u64, p, p, u32, u32, p, p, p],
             "sssp_set_tuning": [p],
             "sssp_get_tuning": [p],
+            "sssp_policy_load": [p, ctypes.c_size_t],
+            "sssp_policy_clear": [],
+            "sssp_policy_features": [u64, u64, u64, u64, u64, u64, u64, p],
+            "sssp_mlp_forward": [p, p, u32, p, p],
+            "sssp_mlp_backward": [p, p, p, p, u32, p, p, p],
+            "sssp_mlp_adam": [p, p, p, p, u32, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                              u32, p],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -263,6 +270,59 @@ def solve_noalloc(n: int, row_off, edges, source: int, criterion: int = IN_OUT, 
     _check(lib().sssp_solve_noalloc(int(n), m, _ptr(row_off), _ptr(edges), int(source), int(criterion), _ptr(out),
                                     ctypes.byref(phases), _stream_ptr(stream)))
     return out, phases.value
+
+
+POLICY_WEIGHTS = 1476
+POLICY_FEATURES = 8
+POLICY_ARMS = 4
+
+
+def policy_load(weights):
+    """sssp_policy_load: numpy float32[1476] or CUDA float32 tensor."""
+    if isinstance(weights, np.ndarray):
+        weights = np.ascontiguousarray(weights, dtype=np.float32)
+        n = weights.size
+    else:
+        n = weights.numel()
+    _check(lib().sssp_policy_load(_ptr(weights), n))
+
+
+def policy_clear():
+    _check(lib().sssp_policy_clear())
+
+
+def policy_features(frontier, n, m, phase, edges_prev, settled_prev, frontier_prev) -> np.ndarray:
+    out = np.zeros(POLICY_FEATURES, np.float32)
+    _check(lib().sssp_policy_features(int(frontier), int(n), int(m), int(phase), int(edges_prev),
+                                      int(settled_prev), int(frontier_prev), _ptr(out)))
+    return out
+
+
+def mlp_forward(w, x, y=None, stream=None):
+    """sssp_mlp_forward on CUDA float32 tensors; returns y [B, 4]."""
+    torch = _torch()
+    B = x.shape[0]
+    if y is None:
+        y = torch.empty(B, POLICY_ARMS, dtype=torch.float32, device=x.device)
+    _check(lib().sssp_mlp_forward(_ptr(w), _ptr(x), B, _ptr(y), _stream_ptr(stream)))
+    return y
+
+
+def mlp_backward(w, x, target, arm, grad=None, loss=None, stream=None):
+    """sssp_mlp_backward on CUDA tensors; returns (grad [1476], loss [1])."""
+    torch = _torch()
+    if grad is None:
+        grad = torch.empty(POLICY_WEIGHTS, dtype=torch.float32, device=x.device)
+    if loss is None:
+        loss = torch.empty(1, dtype=torch.float32, device=x.device)
+    _check(lib().sssp_mlp_backward(_ptr(w), _ptr(x), _ptr(target), _ptr(arm), x.shape[0], _ptr(grad), _ptr(loss),
+                                   _stream_ptr(stream)))
+    return grad, loss
+
+
+def mlp_adam(w, grad, m1, m2, lr, step, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    _check(lib().sssp_mlp_adam(_ptr(w), _ptr(grad), _ptr(m1), _ptr(m2), w.numel(), float(lr), float(beta1),
+                               float(beta2), float(eps), int(step), _stream_ptr(stream)))
 
 
 def _ptr_array(objs):

@@ -42,8 +42,8 @@ struct GraphView {
 // distance (with the settled flag, see kSettledBit) and the minima the
 // criteria compare it with, in one 16-byte load.  d is updated with 64-bit
 // atomicMin / red.min.
-//   im: in-minimum  (static, or the dynamic one when IN-SIMPLE maintains it)
-//   om: out-minimum (static)
+//   im: static in-minimum
+//   om: static out-minimum
 struct __align__(16) VRec {
   unsigned long long d;
   uint32_t im;
@@ -66,9 +66,10 @@ struct GridBarrier {
   unsigned int pad;
 };
 
-// Per-phase accumulators, triple-buffered: slot k % 3 belongs to phase k.
-// It is reset at the top of phase k - 2, filled during phase k - 1 (the
-// thresholds and queue of phase k) and phase k (relax list), and read in phase k.
+// Per-phase accumulators in a ring of 4: slot k % 4 belongs to phase k.  It is
+// reset at the top of phase k - 2, filled during phase k - 1 (the thresholds
+// and queue of phase k) and phase k (relax list, counts), read in phase k and,
+// for the policy's features, in phase k + 1.
 struct PhaseSlot {
   unsigned long long min_d;       // fused thresholds of this phase (from phase k-1)
   unsigned long long min_out;
@@ -78,12 +79,13 @@ struct PhaseSlot {
   unsigned int qcount;            // |F| of this phase
   unsigned int argmin;            // DIJK: lowest id of minimum d
   unsigned int settled_now;       // |S'| of this phase
-  unsigned int pad;
+  unsigned int arm;               // arm the phase ran with (policy index << 8 | dense)
+  unsigned long long t_start;     // %globaltimer when the phase began (trace)
 };
 
 // Per-solve control block in device memory (zeroed before each launch).
 struct Ctl {
-  PhaseSlot slot[3];
+  PhaseSlot slot[4];
   unsigned long long phases, sum_f, settled, relaxed;
   int err;                  // sssp_status recorded by a device-side failure
   unsigned int gate;        // solo mode: bumped when the leader hands back to the group
@@ -102,6 +104,7 @@ struct SolveWS {
   SpEnt* sp;               // [n] relax list
   uint32_t* cur_out;       // [n] out-row cursor (dynamic out-minimum), or nullptr
   uint32_t* cur_in;        // [n] in-row cursor (dynamic in-minimum), or nullptr
+  uint32_t* im_dyn;        // [n] dynamic in-minimum of fringe vertices (IN-SIMPLE phases), or nullptr
   unsigned long long* dist;  // [n] output distances
   Ctl* ctl;
   uint32_t* settle_phase;  // [n] optional

@@ -44,6 +44,7 @@
 
 #include "engine.h"
 #include "internal.h"
+#include "policy.cuh"
 
 namespace sssp {
 
@@ -67,6 +68,7 @@ struct Grp {
 struct Arm {
   bool in_simple;
   bool dense;
+  int index;  // policy arm (0..3), -1 without a policy
 };
 
 // Number of relax-list entries whose base is <= x (bases strictly increasing),
@@ -144,7 +146,6 @@ __device__ __forceinline__ Shared carve(unsigned char* smem) {
 struct Mode {
   bool fused;        // thresholds accumulated in B and C
   bool use_in;       // some IN criterion
-  bool in_maintain;  // dynamic in-minima kept exact in step C (fused kind)
   bool use_out;
   bool out_dyn;      // OUT-SIMPLE (three-step kind)
   bool dijk;
@@ -158,7 +159,7 @@ __device__ __forceinline__ Mode mode_of(uint32_t crit, bool has_cur_in) {
   m.fused = !m.out_dyn && !m.dijk;
   const bool policy = (crit & SSSP_POLICY_LEARNED) != 0;
   m.use_in = (crit & (SSSP_IN_STATIC | SSSP_IN_SIMPLE)) != 0 || policy;
-  m.in_maintain = m.fused && has_cur_in && ((crit & SSSP_IN_SIMPLE) != 0 || policy);
+  (void)has_cur_in;
   return m;
 }
 
@@ -172,7 +173,35 @@ __device__ __forceinline__ Arm arm_for(const SolveParams& p, uint32_t nF) {
   Arm a;
   a.in_simple = (p.crit & SSSP_IN_SIMPLE) != 0;
   a.dense = (p.crit & SSSP_FRONTIER_DENSE) != 0 || ((p.crit & SSSP_FRONTIER_AUTO) && nF > (p.g.n >> 2));
+  a.index = -1;
   return a;
+}
+
+// Arm of phase k: from the criterion mask, or (SSSP_POLICY_LEARNED) from the
+// policy network on the phase-start features, evaluated by warp 0 of the block
+// and shared through shared memory.  Every thread of the block calls it; every
+// block computes the same arm from the same inputs.
+__device__ Arm choose_arm(const SolveParams& p, uint64_t k, uint32_t nF, uint64_t e_prev, uint64_t s_prev,
+                          uint64_t f_prev) {
+  if (!(p.crit & SSSP_POLICY_LEARNED) || p.policy == nullptr) return arm_for(p, nF);
+  __shared__ int s_arm;
+  if ((threadIdx.x >> 5) == 0) {
+    float f[kPolFeat], y[kPolArms];
+    policy_features(f, nF, p.g.n, p.g.m, k, e_prev, s_prev, f_prev);
+    policy_forward_warp(p.policy, f, y);
+    if (threadIdx.x == 0) s_arm = policy_pick(y, p.ws.cur_in != nullptr);
+  }
+  __syncthreads();
+  Arm a;
+  a.index = s_arm;
+  a.in_simple = a.index >= 2;
+  a.dense = (a.index & 1) != 0;
+  __syncthreads();
+  return a;
+}
+
+__device__ __forceinline__ uint32_t arm_code(const Arm& a, bool solo) {
+  return (a.dense ? 1u : 0u) | (solo ? 2u : 0u) | (a.index >= 0 ? ((uint32_t)a.index << 8) | 0x80u : 0u);
 }
 
 __device__ __forceinline__ void reset_slot(PhaseSlot* s) {
@@ -181,6 +210,7 @@ __device__ __forceinline__ void reset_slot(PhaseSlot* s) {
   s->qcount = 0;
   s->argmin = kInf32;
   s->settled_now = 0;
+  s->arm = 0;
 }
 
 // Relaxation of one edge (u -> t) with d[u] = du (step C, any mode): one
@@ -217,10 +247,6 @@ __device__ __forceinline__ void relax_edge(const SolveParams& p, const Mode& md,
       }
     }
   }
-  if (md.in_maintain) {
-    const uint32_t im = in_min_dynamic(p.g, w, t, true);
-    if (im != rt.im) w.vrec[t].im = im;
-  }
 }
 
 // ---------------------------------------------------------------------------
@@ -240,14 +266,15 @@ __device__ bool phase_select(const SolveParams& p, const Grp& grp, const Mode& m
   const int cur = (int)((k - 1) & 1);
   const uint32_t* Q = w.q[cur];
   uint32_t* Qn = w.q[cur ^ 1];
-  PhaseSlot* S0 = &ctl->slot[k % 3];
-  PhaseSlot* S1 = &ctl->slot[(k + 1) % 3];
+  PhaseSlot* S0 = &ctl->slot[k % 4];
+  PhaseSlot* S1 = &ctl->slot[(k + 1) % 4];
   const uint32_t nF = ldcg_u32(&S0->qcount);
   const bool dense = arm.dense;
   const bool in_dyn = md.use_in && arm.in_simple && w.cur_in != nullptr;
   if (leader) {
-    reset_slot(&ctl->slot[(k + 2) % 3]);
+    reset_slot(&ctl->slot[(k + 2) % 4]);
     st.sum_f += nF;
+    if (w.trace) S0->t_start = globaltimer_ns();
   }
 
   // ---- thresholds
@@ -255,6 +282,21 @@ __device__ bool phase_select(const SolveParams& p, const Grp& grp, const Mode& m
   if (md.fused) {
     minD = ldcg_u64(&S0->min_d);
     minOut = ldcg_u64(&S0->min_out);
+    if (in_dyn) {
+      // A': dynamic in-minima against S at the start of the phase (no vertex of
+      // this phase is marked before the barrier).  Cursors only move forward,
+      // so advancing them lazily here is exact.
+      if (dense) {
+        for (uint64_t v = gtid; v < n; v += gthreads)
+          if (ldcg_u8(&w.status[v]) == kF) w.im_dyn[v] = in_min_dynamic(g, w, (uint32_t)v, false);
+      } else {
+        for (uint64_t i = gtid; i < nF; i += gthreads) {
+          const uint32_t v = ldcg_u32(&Q[i]);
+          w.im_dyn[v] = in_min_dynamic(g, w, v, false);
+        }
+      }
+      if (!grp.sync()) return false;
+    }
   } else {
     // A: thresholds over the phase-start state, advancing cursors lazily
     unsigned long long lmin_d = kInf64, lmin_out = kInf64;
@@ -268,7 +310,7 @@ __device__ bool phase_select(const SolveParams& p, const Grp& grp, const Mode& m
           lmin_out = x < lmin_out ? x : lmin_out;
         }
       }
-      if (in_dyn) w.vrec[v].im = in_min_dynamic(g, w, v, false);
+      if (in_dyn) w.im_dyn[v] = in_min_dynamic(g, w, v, false);
     };
     if (dense) {
       for (uint64_t v = gtid; v < n; v += gthreads)
@@ -318,8 +360,7 @@ __device__ bool phase_select(const SolveParams& p, const Grp& grp, const Mode& m
       const VRec r = ldcg_vrec(&w.vrec[v]);
       dv = r.d;
       if (md.use_in) {
-        // record im is the dynamic minimum when maintained, else the static one
-        const uint32_t im = (in_dyn || !md.in_maintain) ? r.im : __ldg(&g.in_min[v]);
+        const uint32_t im = in_dyn ? ldcg_u32(&w.im_dyn[v]) : r.im;
         sel = (im == kInf32) || dv <= minD + im;
       }
       if (!sel && md.use_out) sel = dv <= minOut;
@@ -382,9 +423,8 @@ __device__ bool phase_relax(const SolveParams& p, const Grp& grp, const Mode& md
   const bool leader = grp.rank == 0 && tid == 0;
   const int cur = (int)((k - 1) & 1);
   uint32_t* Qn = w.q[cur ^ 1];
-  PhaseSlot* S0 = &ctl->slot[k % 3];
-  PhaseSlot* S1 = &ctl->slot[(k + 1) % 3];
-  const unsigned long long t0 = leader ? globaltimer_ns() : 0;
+  PhaseSlot* S0 = &ctl->slot[k % 4];
+  PhaseSlot* S1 = &ctl->slot[(k + 1) % 4];
   unsigned long long pd = kInf64, po = kInf64;
   const unsigned long long packed = ldcg_u64(&S0->relax_packed);
   const uint32_t nS = (uint32_t)(packed >> 32);
@@ -435,7 +475,9 @@ __device__ bool phase_relax(const SolveParams& p, const Grp& grp, const Mode& md
     st.relaxed += E;
     st.phases = k;
     if (w.trace && k <= w.trace_cap) {
-      const bool in_dyn = md.use_in && arm.in_simple && w.cur_in != nullptr;
+      const uint32_t code = ldcg_u32(&S0->arm);
+      const bool in_dyn = md.use_in && w.cur_in != nullptr &&
+                          ((code & 0x80u) ? ((code >> 8) >= 2) : arm.in_simple);
       sssp_phase_record r;
       r.frontier = ldcg_u32(&S0->qcount);
       r.settled = settled_now;
@@ -445,8 +487,8 @@ __device__ bool phase_relax(const SolveParams& p, const Grp& grp, const Mode& md
       uint32_t c = p.crit & SSSP_CRITERIA_MASK;
       if (md.use_in) c = (c & ~(uint32_t)(SSSP_IN_STATIC | SSSP_IN_SIMPLE)) | (in_dyn ? SSSP_IN_SIMPLE : SSSP_IN_STATIC);
       r.criterion = c;
-      r.arm = (arm.dense ? 1u : 0u) | (grp.size == 1 ? 2u : 0u);
-      r.t_start_ns = t0;
+      r.arm = ldcg_u32(&S0->arm);
+      r.t_start_ns = ldcg_u64(&S0->t_start);
       r.t_end_ns = globaltimer_ns();
       r.reserved = 0;
       w.trace[k - 1] = r;
@@ -457,7 +499,11 @@ __device__ bool phase_relax(const SolveParams& p, const Grp& grp, const Mode& md
 
 __device__ __forceinline__ bool run_phase(const SolveParams& p, const Grp& grp, const Mode& md, uint64_t k,
                                           const Shared& sh, Stats& st) {
-  const Arm arm = arm_for(p, ldcg_u32(&p.ws.ctl->slot[k % 3].qcount));
+  const PhaseSlot* prev = &p.ws.ctl->slot[(k + 3) % 4];
+  const Arm arm = choose_arm(p, k, ldcg_u32(&p.ws.ctl->slot[k % 4].qcount),
+                             (uint32_t)ldcg_u64(&prev->relax_packed), ldcg_u32(&prev->settled_now),
+                             ldcg_u32(&prev->qcount));
+  if (grp.rank == 0 && threadIdx.x == 0) p.ws.ctl->slot[k % 4].arm = arm_code(arm, grp.size == 1);
   if (!phase_select(p, grp, md, arm, k, sh, st)) return false;
   return phase_relax(p, grp, md, arm, k, sh, st);
 }
@@ -498,9 +544,15 @@ __device__ uint64_t solo_episode(const SolveParams& p, const Mode& md, uint64_t 
   *handoff = false;
 
   const uint32_t cap = p.solo_max < kSoloCap ? p.solo_max : kSoloCap;
-  uint32_t nF = ldcg_u32(&ctl->slot[k % 3].qcount);
-  unsigned long long minD = ldcg_u64(&ctl->slot[k % 3].min_d);
-  unsigned long long minOut = ldcg_u64(&ctl->slot[k % 3].min_out);
+  // counters of the previous phase (policy features)
+  uint64_t e_prev = (uint32_t)ldcg_u64(&ctl->slot[(k + 3) % 4].relax_packed);
+  uint64_t s_prev = ldcg_u32(&ctl->slot[(k + 3) % 4].settled_now);
+  uint64_t f_prev = ldcg_u32(&ctl->slot[(k + 3) % 4].qcount);
+  uint32_t nF = ldcg_u32(&ctl->slot[k % 4].qcount);
+  Arm arm{false, false, -1};
+  unsigned int since_pick = 0;
+  unsigned long long minD = ldcg_u64(&ctl->slot[k % 4].min_d);
+  unsigned long long minOut = ldcg_u64(&ctl->slot[k % 4].min_out);
   {
     const uint32_t* gq = w.q[(k - 1) & 1];
     uint32_t* sq = ((k - 1) & 1) ? sqb : sqa;
@@ -511,7 +563,10 @@ __device__ uint64_t solo_episode(const SolveParams& p, const Mode& md, uint64_t 
     const uint32_t* sq = cur ? sqb : sqa;
     uint32_t* sqn = cur ? sqa : sqb;
     uint32_t* gqn = w.q[cur ^ 1];
-    const Arm arm = arm_for(p, nF);
+    // the policy is evaluated on the first phase of the episode and every 4th
+    // phase after it (the choice is logged per phase either way)
+    if (since_pick == 0) arm = choose_arm(p, k, nF, e_prev, s_prev, f_prev);
+    since_pick = (since_pick + 1) & 3u;
     const bool in_dyn = md.use_in && arm.in_simple && w.cur_in != nullptr;
     unsigned long long t0 = 0;
     if (tid == 0) {
@@ -534,7 +589,7 @@ __device__ uint64_t solo_episode(const SolveParams& p, const Mode& md, uint64_t 
         const uint32_t i = i0 + j * nthr;
         if (i < nF) {
           r_d[i] = r[j].d;
-          r_im[i] = (in_dyn || !md.in_maintain) ? r[j].im : __ldg(&g.in_min[sq[i]]);
+          r_im[i] = in_dyn ? in_min_dynamic(g, w, sq[i], false) : r[j].im;
           r_om[i] = r[j].om;
         }
       }
@@ -664,16 +719,17 @@ __device__ uint64_t solo_episode(const SolveParams& p, const Mode& md, uint64_t 
       for (uint32_t j = tid; j < nk; j += nthr) gqn[j] = sqn[j];
       if (tid == 0) {
         st.sum_f += nF;
-        PhaseSlot* S0 = &ctl->slot[k % 3];
-        PhaseSlot* S1 = &ctl->slot[(k + 1) % 3];
+        PhaseSlot* S0 = &ctl->slot[k % 4];
+        PhaseSlot* S1 = &ctl->slot[(k + 1) % 4];
         reset_slot(S0);
         reset_slot(S1);
-        reset_slot(&ctl->slot[(k + 2) % 3]);
+        reset_slot(&ctl->slot[(k + 2) % 4]);
         S0->qcount = nF;
         S0->min_d = minD;
         S0->min_out = minOut;
         S0->relax_packed = packed;
         S0->settled_now = s_settled;
+        S0->arm = arm_code(arm, true);
         S1->qcount = kept;
         S1->min_d = s_thr_d;
         S1->min_out = s_thr_o;
@@ -737,7 +793,7 @@ __device__ uint64_t solo_episode(const SolveParams& p, const Mode& md, uint64_t 
         uint32_t c = p.crit & SSSP_CRITERIA_MASK;
         if (md.use_in) c = (c & ~(uint32_t)(SSSP_IN_STATIC | SSSP_IN_SIMPLE)) | (in_dyn ? SSSP_IN_SIMPLE : SSSP_IN_STATIC);
         r.criterion = c;
-        r.arm = 2u;
+        r.arm = arm_code(arm, true);
         r.t_start_ns = t0;
         r.t_end_ns = globaltimer_ns();
         r.reserved = 0;
@@ -746,6 +802,9 @@ __device__ uint64_t solo_episode(const SolveParams& p, const Mode& md, uint64_t 
     }
     minD = s_thr_d;
     minOut = s_thr_o;
+    e_prev = E;
+    s_prev = s_settled;
+    f_prev = nF;
     nF = nFn;
     ++k;
     __syncthreads();  // shared counters are read before the next phase resets them
@@ -759,12 +818,16 @@ __device__ uint64_t solo_episode(const SolveParams& p, const Mode& md, uint64_t 
     for (uint32_t i = tid; i < ns; i += nthr) gq[i] = sq[i];
   }
   if (tid == 0) {
-    PhaseSlot* S0 = &ctl->slot[k % 3];
+    PhaseSlot* S0 = &ctl->slot[k % 4];
     reset_slot(S0);
-    reset_slot(&ctl->slot[(k + 1) % 3]);
+    reset_slot(&ctl->slot[(k + 1) % 4]);
     S0->qcount = nF;
     S0->min_d = minD;
     S0->min_out = minOut;
+    PhaseSlot* Sp = &ctl->slot[(k + 3) % 4];  // the last solo phase, for the policy's features
+    Sp->relax_packed = e_prev;
+    Sp->settled_now = (uint32_t)s_prev;
+    Sp->qcount = (uint32_t)f_prev;
   }
   __threadfence();
   __syncthreads();
@@ -804,7 +867,7 @@ __device__ void solve_body(const SolveParams& p, const Grp& grp, unsigned char* 
       asm volatile("prefetch.global.L2::evict_last [%0];" ::"l"(base + l * 128));
   }
   if (leader) {
-    for (int j = 0; j < 3; ++j) reset_slot(&ctl->slot[j]);
+    for (int j = 0; j < 4; ++j) reset_slot(&ctl->slot[j]);
     ctl->heartbeat = 0;
     ctl->next_phase = 0;
     ctl->resume_relax = 0;
@@ -827,7 +890,7 @@ __device__ void solve_body(const SolveParams& p, const Grp& grp, unsigned char* 
   unsigned int episodes = 0;
   uint64_t k = 1;
   for (;;) {
-    uint32_t nF = ldcg_u32(&ctl->slot[k % 3].qcount);
+    uint32_t nF = ldcg_u32(&ctl->slot[k % 4].qcount);
     if (nF == 0) break;
     const bool fast_solo = md.fused && !dense_forced && nF <= solo_cap;
     const bool generic_solo = !md.fused && grp.size > 1 && nF <= p.solo_max;
@@ -845,7 +908,7 @@ __device__ void solve_body(const SolveParams& p, const Grp& grp, unsigned char* 
             run_phase(p, solo, md, k, sh, st);
             ++k;
             if (tid == 0) ctl->heartbeat = k;
-            nF = ldcg_u32(&ctl->slot[k % 3].qcount);
+            nF = ldcg_u32(&ctl->slot[k % 4].qcount);
           }
         }
         if (grp.size > 1) {
@@ -872,7 +935,7 @@ __device__ void solve_body(const SolveParams& p, const Grp& grp, unsigned char* 
       }
       ++episodes;
       if (resume_relax) {
-        const Arm arm = arm_for(p, ldcg_u32(&ctl->slot[k % 3].qcount));
+        const Arm arm = arm_for(p, ldcg_u32(&ctl->slot[k % 4].qcount));
         if (!phase_relax(p, grp, md, arm, k, sh, st)) return;
         ++k;
       }
@@ -942,6 +1005,7 @@ __global__ void __launch_bounds__(kThreads) k_solve_batch(const BatchItem* items
     p.wait_ns = wait_ns;
     p.solo_max = solo_max;
     p.solo_edges = solo_edges;
+    p.policy = nullptr;
     solve_body(p, grp, smem);
     if (*(volatile int*)err != 0) return;
     if (rank == 0 && threadIdx.x == 0) {
@@ -975,10 +1039,14 @@ sssp_status ensure_kernel_attrs() {
 
 sssp_status check_crit(const sssp_graph* g, uint32_t crit) {
   const uint32_t known = SSSP_IN_STATIC | SSSP_OUT_STATIC | SSSP_IN_SIMPLE | SSSP_OUT_SIMPLE | SSSP_DIJK |
-                         SSSP_FRONTIER_DENSE | SSSP_FRONTIER_AUTO;
+                         SSSP_FRONTIER_DENSE | SSSP_FRONTIER_AUTO | SSSP_POLICY_LEARNED;
   if ((crit & SSSP_CRITERIA_MASK) == 0) return fail(SSSP_ERR_INVALID_ARG, "criterion mask has no criterion bit");
-  if (crit & SSSP_POLICY_LEARNED) return fail(SSSP_ERR_UNSUPPORTED, "no phase policy is loaded");
   if (crit & ~known) return fail(SSSP_ERR_INVALID_ARG, "unknown criterion bits 0x%x", crit & ~known);
+  if (crit & SSSP_POLICY_LEARNED) {
+    if (!policy_weights()) return fail(SSSP_ERR_UNSUPPORTED, "no phase policy is loaded on this device");
+    if ((crit & SSSP_CRITERIA_MASK) != (SSSP_IN_STATIC | SSSP_OUT_STATIC))
+      return fail(SSSP_ERR_INVALID_ARG, "SSSP_POLICY_LEARNED takes IN_STATIC | OUT_STATIC as its fallback arm");
+  }
   if ((crit & SSSP_IN_SIMPLE) && !g->rrow_off)
     return fail(SSSP_ERR_UNSUPPORTED, "IN-SIMPLE needs a graph built with SSSP_GRAPH_REVERSE");
   return SSSP_OK;
@@ -1009,6 +1077,7 @@ void workspace_free(Workspace* ws) {
   cudaFree(ws->sp);
   cudaFree(ws->cur_out);
   cudaFree(ws->cur_in);
+  cudaFree(ws->im_dyn);
   cudaFree(ws->dist);
   cudaFree(ws->ctl);
   cudaFreeHost(ws->ctl_host);
@@ -1025,7 +1094,8 @@ sssp_status workspace_alloc(uint32_t n, bool want_cursors, bool want_dist, Works
     workspace_free(ws);
     return s;
   }
-  if (want_cursors && ((s = dev_alloc(&ws->cur_out, n)) || (s = dev_alloc(&ws->cur_in, n)))) {
+  if (want_cursors && ((s = dev_alloc(&ws->cur_out, n)) || (s = dev_alloc(&ws->cur_in, n)) ||
+                       (s = dev_alloc(&ws->im_dyn, n)))) {
     workspace_free(ws);
     return s;
   }
@@ -1063,6 +1133,7 @@ SolveWS ws_view(Workspace* ws, unsigned long long* dist, uint32_t crit, bool has
   w.dist = dist ? dist : ws->dist;
   w.cur_out = (crit & SSSP_OUT_SIMPLE) ? ws->cur_out : nullptr;
   w.cur_in = ((crit & (SSSP_IN_SIMPLE | SSSP_POLICY_LEARNED)) && has_reverse) ? ws->cur_in : nullptr;
+  w.im_dyn = w.cur_in ? ws->im_dyn : nullptr;
   w.ctl = ws->ctl;
   return w;
 }
@@ -1101,6 +1172,7 @@ sssp_status solve_one(sssp_graph* g, uint32_t source, uint32_t crit, uint64_t* d
   p.wait_ns = wait_limit_ns();
   p.solo_max = solo_max();
   p.solo_edges = solo_edges();
+  p.policy = (crit & SSSP_POLICY_LEARNED) ? policy_weights() : nullptr;
 
   const int blocks = blocks_for(g->n);
   SSSP_CUDA_TRY(cudaMemsetAsync(ws->ctl, 0, sizeof(Ctl), st));
@@ -1193,6 +1265,7 @@ sssp_status batch_build(sssp_graph* const* graphs, const uint32_t* sources, uint
                         uint64_t* const* dist_out, uint64_t* phases_dev, uint32_t bpg, cudaStream_t st,
                         sssp_batch** out) {
   if (!graphs || !sources || !dist_out || count == 0) return fail(SSSP_ERR_INVALID_ARG, "empty or NULL batch");
+  if (crit & SSSP_POLICY_LEARNED) return fail(SSSP_ERR_UNSUPPORTED, "batches run without the phase policy");
   for (uint32_t i = 0; i < count; ++i) {
     if (!graphs[i]) return fail(SSSP_ERR_INVALID_ARG, "graph %u is NULL", i);
     if (sources[i] >= graphs[i]->n) return fail(SSSP_ERR_INVALID_ARG, "source of solve %u out of range", i);

@@ -33,7 +33,8 @@ struct SolveParams {
   uint32_t crit;
   unsigned long long wait_ns;
   uint32_t solo_max;    // largest fringe run by one block alone (0 = never)
-  uint32_t solo_edges;  // largest total fringe out-degree run by one block alone
+  uint32_t solo_edges;  // relax edges above which a solo phase hands off to the group
+  const float* policy;  // policy network weights (device) or nullptr
 };
 
 // One whole solve per cooperative launch (all blocks co-resident), kThreads

@@ -24,6 +24,9 @@ uint32_t batch_blocks_per_solve();
 uint32_t grid_blocks();
 uint32_t solo_edges();
 
+// Policy network weights loaded on the current device, or nullptr.
+const float* policy_weights();
+
 // Returns true if p points to device (or managed) memory.
 bool is_device_pointer(const void* p);
 
@@ -75,6 +78,7 @@ struct Workspace {
   SpEnt* sp;
   uint32_t* cur_out;
   uint32_t* cur_in;
+  uint32_t* im_dyn;
   unsigned long long* dist;  // used when the caller's distance buffer is host memory
   Ctl* ctl;
   Ctl* ctl_host;  // pinned mirror for read-back

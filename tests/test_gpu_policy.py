@@ -1,0 +1,159 @@
+"""Per-phase policy network on the GPU: the FP32 training kernels against the
+float64 oracle, exactness of solves that switch arms every phase (the
+simulator replays the logged schedule), and what a trained network gains."""
+import time
+
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+from oracle import mlp as omlp
+
+sp = pytest.importorskip("paper_1903_12085_gb300")
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _device():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+    yield
+    sp.policy_clear()
+    sp.set_tuning()
+
+
+def _batch(seed, B=777):
+    rng = np.random.default_rng(seed)
+    x = rng.uniform(0, 1, size=(B, 8)).astype(np.float32)
+    t = rng.normal(0, 2, size=B).astype(np.float32)
+    a = rng.integers(0, 4, size=B).astype(np.uint32)
+    return x, t, a
+
+
+def _cuda(a):
+    if a.dtype == np.uint32:
+        a = a.view(np.int32)
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def test_forward_matches_oracle():
+    w = omlp.init(1).astype(np.float32)
+    x, _, _ = _batch(2)
+    y = sp.mlp_forward(_cuda(w), _cuda(x)).cpu().numpy()
+    ref, _ = omlp.forward(w.astype(np.float64), x.astype(np.float64))
+    assert np.allclose(y, ref, rtol=1e-4, atol=1e-5)
+
+
+def test_backward_matches_oracle():
+    w = omlp.init(3).astype(np.float32)
+    x, t, a = _batch(4)
+    g, loss = sp.mlp_backward(_cuda(w), _cuda(x), _cuda(t), _cuda(a))
+    g = g.cpu().numpy()
+    L, gref = omlp.backward(w.astype(np.float64), x.astype(np.float64), t.astype(np.float64), a)
+    assert np.isclose(float(loss.item()), L, rtol=1e-4)
+    scale = np.abs(gref).max()
+    assert np.abs(g - gref).max() <= 1e-4 * scale, np.abs(g - gref).max() / scale
+    # deterministic: a second call gives the same bits
+    g2, _ = sp.mlp_backward(_cuda(w), _cuda(x), _cuda(t), _cuda(a))
+    assert np.array_equal(g, g2.cpu().numpy())
+
+
+def test_adam_step_matches_formula():
+    rng = np.random.default_rng(5)
+    w = rng.normal(size=1476).astype(np.float32)
+    g = rng.normal(size=1476).astype(np.float32)
+    m1 = rng.normal(size=1476).astype(np.float32) * 0.1
+    m2 = np.abs(rng.normal(size=1476)).astype(np.float32) * 0.1
+    W, G, M1, M2 = (_cuda(v.copy()) for v in (w, g, m1, m2))
+    sp.mlp_adam(W, G, M1, M2, lr=0.01, step=3)
+    b1, b2, eps = 0.9, 0.999, 1e-8
+    a = b1 * m1.astype(np.float64) + (1 - b1) * g
+    b = b2 * m2.astype(np.float64) + (1 - b2) * g.astype(np.float64) ** 2
+    ref = w - 0.01 * (a / (1 - b1 ** 3)) / (np.sqrt(b / (1 - b2 ** 3)) + eps)
+    assert np.allclose(W.cpu().numpy(), ref, rtol=1e-5, atol=1e-6)
+
+
+TUNINGS = [(4096, 0, 2048), (0, 3, 0), (8, 3, 24)]
+
+
+@pytest.mark.parametrize("tune", TUNINGS, ids=["default", "grid3", "solo3_handoff"])
+def test_policy_solves_are_exact_and_replayable(tune):
+    """A random network switches arms from phase to phase; distances equal
+    Dijkstra's and the simulator, fed the logged per-phase criteria, settles
+    exactly the same vertices in every phase."""
+    sp.set_tuning(solo_max_frontier=tune[0], grid_blocks=tune[1], solo_max_edges=tune[2])
+    try:
+        for seed in range(3):
+            sp.policy_load(omlp.init(100 + seed, scale=1.0).astype(np.float32))
+            for wl in [gg.workload(1, shrink=2), gg.workload(3, shrink=12), gg.workload(2, shrink=10)]:
+                gi, s = wl.solves[0]
+                g = wl.graphs[gi]
+                G = sp.Graph.from_csr(g, reverse=True)
+                d, st, settle, tr = sp.solve_trace(G, s, sp.IN_OUT | sp.POLICY_LEARNED, trace_cap=1 << 20)
+                ref = oracle.dijkstra(g, s)
+                assert (sp.as_uint64(d) == ref).all()
+                sched = tr["criterion"].astype(np.uint32)
+                assert set(np.unique(sched)) <= {sp.IN_OUT, sp.IN_SIMPLE | sp.OUT_STATIC}
+                assert ((tr["arm"] & 0x80) != 0).all()
+                sim = oracle.simulate(g, s, sp.IN_OUT, schedule=sched, dist_ref=ref)
+                assert st["phases"] == sim.phases
+                assert (settle == sim.settle_phase).all()
+                assert st["sum_frontier"] == sim.sum_f
+    finally:
+        sp.set_tuning()
+
+
+def test_policy_requires_a_loaded_network_and_the_fallback_criterion():
+    g = gg.workload(1, shrink=4).graphs[0]
+    G = sp.Graph.from_csr(g, reverse=True)
+    sp.policy_clear()
+    with pytest.raises(sp.SsspError) as e:
+        sp.solve(G, 0, sp.IN_OUT | sp.POLICY_LEARNED)
+    assert e.value.status == 6
+    sp.policy_load(omlp.init(1).astype(np.float32))
+    with pytest.raises(sp.SsspError) as e:
+        sp.solve(G, 0, sp.SIMPLE | sp.POLICY_LEARNED)
+    assert e.value.status == 1
+
+
+def _time(G, s, crit, reps=5):
+    out = torch.empty(G.n, dtype=torch.int64, device="cuda")
+    sp.solve(G, s, crit, out=out)
+    ts = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        _, ph = sp.solve(G, s, crit, out=out)
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return float(np.median(ts)), ph
+
+
+def test_trained_policy_gain(capsys):
+    """Train on small graphs of every family, evaluate on larger held-out ones:
+    the trained network's solve time against the fixed IN+OUT method."""
+    from paper_1903_12085_gb300 import policy as pol
+
+    w, hist = pol.fit_and_load()
+    assert hist[-1][1] < hist[0][1]  # training lowers the loss
+    rows = []
+    for k, shrink in [(3, 4), (5, 4), (1, 0), (2, 4)]:
+        wl = gg.workload(k, shrink=shrink)
+        gi, s = wl.solves[0]
+        G = sp.Graph.from_csr(wl.graphs[gi], reverse=True)
+        t_fix, p_fix = _time(G, s, sp.IN_OUT)
+        t_learn, p_learn = _time(G, s, sp.IN_OUT | sp.POLICY_LEARNED)
+        rows.append((wl.name, t_fix, p_fix, t_learn, p_learn))
+    with capsys.disabled():
+        print("\npolicy gain (held-out graphs): name, IN+OUT ms, phases, learned ms, phases, speedup")
+        for r in rows:
+            print(f"  {r[0]:24s} {r[1]:9.3f} {r[2]:7d} {r[3]:9.3f} {r[4]:7d} {r[1] / r[3]:6.2f}x")
+    total_fix = sum(r[1] for r in rows)
+    total_learn = sum(r[3] for r in rows)
+    assert total_learn <= 1.10 * total_fix
