@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--criterion", default="in_out", choices=["in_out", "simple", "learned"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-policy", action="store_true", help="skip training/timing the learned policy")
+    ap.add_argument("--batch-sources", type=int, default=152,
+                    help="sources of the batched leg (one persistent launch), 0 to skip")
     return ap.parse_args()
 
 
@@ -264,6 +267,72 @@ def main():
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": None, "peak_kind": peak_kind, "kernel": "k_solve_grid" if not batched else "k_solve_batch"}
 
+    # ---- learned per-phase policy (trained here on small graphs, by the
+    # library's own FP32 kernels), same workload and timing rules
+    learned = None
+    if not batched and not args.no_policy and args.criterion == "in_out":
+        from paper_1903_12085_gb300 import policy as pol
+        t0 = time.perf_counter()
+        _, hist = pol.fit_and_load()
+        train_s = time.perf_counter() - t0
+        Gr = [sp.Graph.from_csr(g, reverse=True) for g in wl.graphs]
+        lcrit = sp.IN_OUT | sp.POLICY_LEARNED
+        lstats = []
+        for k in range(len(wl.solves)):
+            gi, s = wl.solves[k]
+            _, st, _, _ = sp.solve_trace(Gr[gi], s, lcrit, settle=False)
+            lstats.append(st)
+        for k in range(args.warmup):
+            gi, s = wl.solves[k % len(wl.solves)]
+            sp.solve(Gr[gi], s, lcrit, out=outs[gi])
+        lev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        ledges = lphases = 0
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush.zero_()
+            gi, s = wl.solves[k % len(wl.solves)]
+            lev[k][0].record(stream)
+            sp.solve(Gr[gi], s, lcrit, out=outs[gi])
+            lev[k][1].record(stream)
+            ledges += lstats[k % len(lstats)]["edges_relaxed"]
+            lphases += lstats[k % len(lstats)]["phases"]
+        torch.cuda.synchronize()
+        lms = sum(a.elapsed_time(b) for a, b in lev)
+        learned = {"value": ws * ledges / (lms * 1e-3) / 1e9, "unit": "GTEPS", "ms_per_step": lms / args.steps,
+                   "phases_per_solve": lphases / args.steps, "speedup_vs_in_out": total_ms / lms,
+                   "train_s": round(train_s, 2), "final_train_loss": hist[-1][1] if hist else None}
+        sp.policy_clear()
+
+    # ---- batched: many sources on the same graph(s) in one persistent launch
+    # captured in a CUDA graph (groups of blocks per solve chosen by the library)
+    batched_leg = None
+    if not batched and args.batch_sources > 0:
+        import graphgen as gg
+        gi0 = wl.solves[0][0]
+        g0 = wl.graphs[gi0]
+        rng_src = [int(gg.splitmix64_nth(0x5EED0B, i) >> 32) * g0.n >> 32 for i in range(args.batch_sources)]
+        rng_src[0] = wl.solves[0][1]
+        B = sp.Batch([G[gi0]] * len(rng_src), rng_src, crit)
+        for _ in range(args.warmup):
+            B.launch()
+        torch.cuda.synchronize()
+        # edges relaxed by each solve = out-degrees of the vertices it reached
+        deg_t = torch.from_numpy(g0.outdeg()).cuda()
+        bedges = int(sum(int(deg_t[o != -1].sum().item()) for o in B.outs))
+        bev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for k in range(args.steps):
+            flush.zero_()
+            bev[k][0].record(stream)
+            B.launch()
+            bev[k][1].record(stream)
+        torch.cuda.synchronize()
+        bms = sum(a.elapsed_time(b) for a, b in bev) / args.steps
+        batched_leg = {"sources": len(rng_src), "ms_per_launch": bms,
+                       "queries_per_s": ws * len(rng_src) / (bms * 1e-3),
+                       "value": ws * bedges / (bms * 1e-3) / 1e9, "unit": "GTEPS",
+                       "speedup_queries_vs_single": (len(rng_src) / bms) / (nsolves / total_ms)}
+        B.close()
+
     # ---- end to end through the public API with host buffers
     e2e = None
     if not batched:
@@ -303,6 +372,7 @@ def main():
                        "prep_ms": prep_ms, "l2": "flushed between steps (2x L2 buffer written)",
                        "parallelism": f"replicas x{ws}"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "learned_policy": learned, "batched": batched_leg,
             "gpu_launches": args.steps, "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
