@@ -221,6 +221,28 @@ __device__ __forceinline__ void block_min2_to_global(unsigned long long a, unsig
   __syncthreads();
 }
 
+// Block-wide exclusive prefix sum of one u32 per thread (blockDim.x a
+// multiple of 32, at most 1024).  scratch: 33 u32 of shared memory.  Returns
+// the thread's exclusive prefix; *total gets the block total (every thread).
+// All threads of the block must call it.
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* scratch, uint32_t* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const uint32_t incl = warp_inclusive_scan(v);
+  if (lane == 31) scratch[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const uint32_t w = lane < nwarps ? scratch[lane] : 0u;
+    const uint32_t wi = warp_inclusive_scan(w);
+    if (lane < nwarps) scratch[lane] = wi - w;
+    if (lane == 31) scratch[32] = wi;
+  }
+  __syncthreads();
+  const uint32_t r = scratch[warp] + incl - v;
+  *total = scratch[32];
+  __syncthreads();
+  return r;
+}
+
 // Warp-aggregated append: every lane of a full warp calls it; lanes with
 // pred=true get consecutive slots of q (one atomicAdd per warp).  A slot at or
 // beyond `cap` is not written; it records SSSP_ERR_INTERNAL in *err instead.

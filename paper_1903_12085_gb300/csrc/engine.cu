@@ -125,20 +125,24 @@ __device__ __forceinline__ uint32_t in_min_dynamic(const GraphView& g, const Sol
 }
 
 struct Shared {
-  unsigned long long* red;  // 64
-  uint32_t* s_base;         // kTile
-  uint32_t* s_row;          // kTile
-  unsigned long long* s_d;  // kTile
-  uint32_t* s_range;        // 2
+  unsigned long long* red;    // 64
+  unsigned long long* bases;  // 2: output offsets reserved by the block
+  uint32_t* s_base;           // kTile
+  uint32_t* s_row;            // kTile
+  unsigned long long* s_d;    // kTile
+  uint32_t* s_range;          // 2
+  uint32_t* scan;             // 34
 };
 
 __device__ __forceinline__ Shared carve(unsigned char* smem) {
   Shared s;
   s.red = reinterpret_cast<unsigned long long*>(smem);
-  s.s_d = s.red + 64;
+  s.bases = s.red + 64;
+  s.s_d = s.bases + 2;
   s.s_base = reinterpret_cast<uint32_t*>(s.s_d + kTile);
   s.s_row = s.s_base + kTile;
   s.s_range = s.s_row + kTile;
+  s.scan = s.s_range + 2;
   return s;
 }
 
@@ -341,26 +345,44 @@ __device__ bool phase_select(const SolveParams& p, const Grp& grp, const Mode& m
     amin = ldcg_u32(&S0->argmin);
   }
 
-  // ---- B: select S', mark settled, build the relax list, compact the rest of F
+  // ---- B: select S', mark settled, build the relax list, compact the rest of F.
+  // Each block takes contiguous chunks of kSelItems * blockDim entries; all of a
+  // thread's record gathers are in flight together, and the chunk's kept
+  // entries and relax-list entries are placed with block scans and one atomic
+  // per chunk and output (coalesced writes, no per-warp contention).
   unsigned long long pd = kInf64, po = kInf64;  // fused partials for phase k+1
   const uint64_t total = dense ? n : nF;
+  const uint64_t chunk = (uint64_t)nthr * kSelItems;
   uint32_t settled_here = 0;
-  for (uint64_t base = gtid & ~31ull; base < total; base += gthreads) {
-    const uint64_t i = base + lane;
-    bool valid = i < total;
-    uint32_t v = 0;
-    if (valid) {
-      v = dense ? (uint32_t)i : ldcg_u32(&Q[i]);
-      if (dense) valid = ldcg_u8(&w.status[v]) == kF;
+  for (uint64_t c0 = (uint64_t)grp.rank * chunk; c0 < total; c0 += (uint64_t)grp.size * chunk) {
+    uint32_t vv[kSelItems];
+    bool ok[kSelItems];
+#pragma unroll
+    for (int j = 0; j < kSelItems; ++j) {
+      const uint64_t i = c0 + (uint64_t)j * nthr + tid;
+      ok[j] = i < total;
+      vv[j] = ok[j] ? (dense ? (uint32_t)i : ldcg_u32(&Q[i])) : 0u;
     }
-    bool sel = false;
-    uint32_t deg = 0, row = 0;
-    unsigned long long dv = 0;
-    if (valid) {
-      const VRec r = ldcg_vrec(&w.vrec[v]);
-      dv = r.d;
+    if (dense) {
+#pragma unroll
+      for (int j = 0; j < kSelItems; ++j)
+        if (ok[j]) ok[j] = ldcg_u8(&w.status[vv[j]]) == kF;
+    }
+    VRec rr[kSelItems];
+#pragma unroll
+    for (int j = 0; j < kSelItems; ++j)
+      if (ok[j]) rr[j] = ldcg_vrec(&w.vrec[vv[j]]);
+    uint32_t selm = 0, keepm = 0;
+    uint2 rd[kSelItems];
+#pragma unroll
+    for (int j = 0; j < kSelItems; ++j) {
+      rd[j] = make_uint2(0, 0);
+      if (!ok[j]) continue;
+      const uint32_t v = vv[j];
+      const unsigned long long dv = rr[j].d;
+      bool sel = false;
       if (md.use_in) {
-        const uint32_t im = in_dyn ? ldcg_u32(&w.im_dyn[v]) : r.im;
+        const uint32_t im = in_dyn ? ldcg_u32(&w.im_dyn[v]) : rr[j].im;
         sel = (im == kInf32) || dv <= minD + im;
       }
       if (!sel && md.use_out) sel = dv <= minOut;
@@ -369,41 +391,59 @@ __device__ bool phase_select(const SolveParams& p, const Grp& grp, const Mode& m
         w.status[v] = kS;
         w.vrec[v].d = dv | kSettledBit;
         if (w.settle_phase) w.settle_phase[v] = (uint32_t)k;
-        const uint2 rd = __ldg(&g.rowdeg[v]);
-        row = rd.x;
-        deg = rd.y;
-      } else if (md.fused) {
-        pd = dv < pd ? dv : pd;
-        if (r.om != kInf32) {
-          const unsigned long long x = dv + r.om;
-          po = x < po ? x : po;
+        rd[j] = __ldg(&g.rowdeg[v]);
+        selm |= 1u << j;
+      } else {
+        keepm |= 1u << j;
+        if (md.fused) {
+          pd = dv < pd ? dv : pd;
+          if (rr[j].om != kInf32) {
+            const unsigned long long x = dv + rr[j].om;
+            po = x < po ? x : po;
+          }
         }
       }
     }
-    // relax list (settled vertices with out-edges): slots and edge range in one atomic
-    const bool rl = sel && deg > 0;
-    const unsigned int rmask = __ballot_sync(0xFFFFFFFFu, rl);
-    if (rmask) {
-      const uint32_t c = rl ? deg : 0;
-      const uint32_t incl = warp_inclusive_scan(c);
-      const uint32_t tot = __shfl_sync(0xFFFFFFFFu, incl, 31);
-      unsigned long long old = 0;
-      if (lane == 0) old = atomicAdd(&S0->relax_packed, ((unsigned long long)__popc(rmask) << 32) | tot);
-      old = __shfl_sync(0xFFFFFFFFu, old, 0);
-      if (rl) {
-        const uint32_t slot = (uint32_t)(old >> 32) + __popc(rmask & ((1u << lane) - 1u));
-        if (slot < n) {
-          const uint32_t base_e = (uint32_t)old + incl - c;
-          *reinterpret_cast<ulonglong2*>(&w.sp[slot]) =
-              make_ulonglong2(dv, (unsigned long long)row | ((unsigned long long)base_e << 32));
-        } else {
+    settled_here += __popc(selm);
+    uint32_t nrel = 0, erel = 0;
+#pragma unroll
+    for (int j = 0; j < kSelItems; ++j)
+      if (((selm >> j) & 1u) && rd[j].y > 0) {
+        ++nrel;
+        erel += rd[j].y;
+      }
+    uint32_t tk, tr, te;
+    const uint32_t pk = block_exclusive_scan(__popc(keepm), sh.scan, &tk);
+    const uint32_t pr = block_exclusive_scan(nrel, sh.scan, &tr);
+    const uint32_t pe = block_exclusive_scan(erel, sh.scan, &te);
+    if (tid == 0) {
+      sh.bases[0] = tk ? atomicAdd(&S1->qcount, tk) : 0u;
+      sh.bases[1] = tr ? atomicAdd(&S0->relax_packed, ((unsigned long long)tr << 32) | te) : 0ull;
+    }
+    __syncthreads();
+    uint32_t kslot = (uint32_t)sh.bases[0] + pk;
+    const unsigned long long rb = sh.bases[1];
+    uint32_t rslot = (uint32_t)(rb >> 32) + pr;
+    uint32_t ebase = (uint32_t)rb + pe;
+#pragma unroll
+    for (int j = 0; j < kSelItems; ++j) {
+      if ((keepm >> j) & 1u) {
+        if (kslot < n) Qn[kslot] = vv[j];
+        else atomicCAS(&ctl->err, 0, (int)SSSP_ERR_INTERNAL);
+        ++kslot;
+      }
+      if (((selm >> j) & 1u) && rd[j].y > 0) {
+        if (rslot < n)
+          *reinterpret_cast<ulonglong2*>(&w.sp[rslot]) =
+              make_ulonglong2(rr[j].d, (unsigned long long)rd[j].x | ((unsigned long long)ebase << 32));
+        else
           atomicCAS(&ctl->err, 0, (int)SSSP_ERR_INTERNAL);
-        }
+        ++rslot;
+        ebase += rd[j].y;
       }
     }
-    warp_append(Qn, &S1->qcount, valid && !sel, v, n, &ctl->err);
-    settled_here += __popc(__ballot_sync(0xFFFFFFFFu, sel));
   }
+  settled_here = __reduce_add_sync(0xFFFFFFFFu, settled_here);
   if (lane == 0 && settled_here) atomicAdd(&S0->settled_now, settled_here);
   if (md.fused) block_min2_to_global(pd, po, &S1->min_d, md.use_out ? &S1->min_out : nullptr, sh.red);
   return grp.sync();
@@ -449,10 +489,12 @@ __device__ bool phase_relax(const SolveParams& p, const Grp& grp, const Mode& md
       sh.s_d[j] = e.d;
     }
     __syncthreads();
-    for (uint32_t eb = e0 + warp * 32; eb < e1; eb += nthr) {
-      const uint32_t e = eb + lane;
-      bool fresh = false;
-      uint32_t t = 0;
+    uint32_t fv[kRelaxItems];
+    uint32_t fmask = 0;
+#pragma unroll
+    for (int it = 0; it < kRelaxItems; ++it) {
+      const uint32_t e = e0 + it * nthr + tid;
+      fv[it] = 0;
       if (e < e1) {
         uint32_t a = 0, b = cnt;  // owner = last j with s_base[j] <= e
         while (b - a > 1) {
@@ -460,11 +502,27 @@ __device__ bool phase_relax(const SolveParams& p, const Grp& grp, const Mode& md
           if (sh.s_base[mid] <= e) a = mid; else b = mid;
         }
         const uint2 ed = __ldg(&g.edges[sh.s_row[a] + (e - sh.s_base[a])]);
-        t = ed.x;
-        relax_edge(p, md, t, ed.y, sh.s_d[a], pd, po, fresh);
+        bool fresh = false;
+        relax_edge(p, md, ed.x, ed.y, sh.s_d[a], pd, po, fresh);
+        if (fresh) {
+          fv[it] = ed.x;
+          fmask |= 1u << it;
+        }
       }
-      warp_append(Qn, &S1->qcount, fresh, t, n, &ctl->err);
     }
+    // vertices new to F: one block scan and one atomic per tile
+    uint32_t tf;
+    const uint32_t pf = block_exclusive_scan(__popc(fmask), sh.scan, &tf);
+    if (tid == 0) sh.bases[0] = tf ? atomicAdd(&S1->qcount, tf) : 0u;
+    __syncthreads();
+    uint32_t fslot = (uint32_t)sh.bases[0] + pf;
+#pragma unroll
+    for (int it = 0; it < kRelaxItems; ++it)
+      if ((fmask >> it) & 1u) {
+        if (fslot < n) Qn[fslot] = fv[it];
+        else atomicCAS(&ctl->err, 0, (int)SSSP_ERR_INTERNAL);
+        ++fslot;
+      }
     __syncthreads();
   }
   if (md.fused) block_min2_to_global(pd, po, &S1->min_d, md.use_out ? &S1->min_out : nullptr, sh.red);

@@ -7,15 +7,16 @@ namespace sssp {
 
 constexpr int kThreads = 512;
 constexpr int kRelaxItems = 4;
+constexpr int kSelItems = 4;  // fringe entries per thread per selection chunk
 constexpr int kTile = kThreads * kRelaxItems;
 // Solo mode (one block runs whole phases with its queues in shared memory):
 // fringe and relax list hold at most kSoloCap entries.
 constexpr uint32_t kSoloCap = 4096;
 constexpr uint32_t kSoloMaxDefault = kSoloCap;     // fringe size limit
 constexpr uint32_t kSoloEdgesDefault = 2048;       // relax edges above which a solo phase hands off
-constexpr size_t kGridSmem = 64 * sizeof(unsigned long long)                               // reduction scratch
+constexpr size_t kGridSmem = 66 * sizeof(unsigned long long)                               // reduction scratch, bases
                              + kTile * (2 * sizeof(uint32_t) + sizeof(unsigned long long))  // relax tile
-                             + 16;
+                             + 36 * sizeof(uint32_t);                                        // range, scan
 constexpr size_t kSoloSmem = 64 * sizeof(unsigned long long)                       // reduction scratch
                              + 2 * kSoloCap * sizeof(uint32_t)                     // two queues
                              + kSoloCap * (2 * sizeof(uint32_t) + sizeof(unsigned long long))  // relax list
