@@ -54,6 +54,32 @@ def parse():
     return ap.parse_args()
 
 
+# DRAM bytes (read + write) of one solve launch, from one ncu capture of this
+# bench's own command (the summaries under profiles/ give the command), keyed by
+# workload name and criterion, with a hash of the engine sources the capture ran
+# on: once the kernel changes the figure no longer applies and is reported null.
+MEASURED_TRAFFIC = {
+    ("grid_1024x1024", "in_out"): (51744256 + 3729152, "efc9c87bd754b90d"),
+}
+ENGINE_SOURCES = ("engine.cu", "engine.h", "common.cuh", "policy.cuh")
+
+
+def engine_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in ENGINE_SOURCES:
+        with open(os.path.join(ROOT, "paper_1903_12085_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(workload: str, criterion: str):
+    t = MEASURED_TRAFFIC.get((workload, criterion))
+    if t is None or t[1] != engine_hash():
+        return None
+    return t[0]
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -118,6 +144,30 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def combine_ranks(dist, device, total_ms: float, counts: dict) -> tuple:
+    """Whole-job figures of a timed region run by every rank of ``dist``.
+
+    Returns (max over ranks of total_ms, {key: sum over ranks}).  The time is
+    the slowest rank's (the job ends when it does); the counts (edges, solves,
+    phases, ...) add up because every rank processed its own units.  With
+    ``dist`` None (one process) the inputs come back unchanged.
+    """
+    if dist is None:
+        return total_ms, dict(counts)
+    import torch
+    keys = sorted(counts)
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    c = torch.tensor([int(counts[k]) for k in keys], dtype=torch.int64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t.item()), {k: int(v) for k, v in zip(keys, c.tolist())}
+
+
+def rank_solve(solves: list, rank: int, k: int):
+    """Solve of step k on this rank: ranks start at different sources."""
+    return solves[(k + rank) % len(solves)]
 
 
 def build_workload(k: int):
@@ -214,13 +264,14 @@ def main():
         outs = [torch.empty(g.n, dtype=torch.int64, device="cuda") for g in wl.graphs]
 
         def step(k):
-            gi, s = wl.solves[k % len(wl.solves)]
+            gi, s = rank_solve(wl.solves, rank, k)
             return sp.solve_trace(G[gi], s, crit, out=outs[gi], settle=False)
 
-    # edges / phases / frontier work per step (deterministic: from one traced pass per solve)
+    # edges / phases / frontier work per step (deterministic: from one traced
+    # pass per solve), indexed like step(k)
     per_solve = []
     for k in range(len(wl.solves)):
-        gi, s = wl.solves[k]
+        gi, s = rank_solve(wl.solves, rank, k)
         _, stats, _, _ = sp.solve_trace(G[gi], s, crit, settle=False)
         per_solve.append(stats)
     for k in range(args.warmup):
@@ -249,23 +300,25 @@ def main():
                 settled += st["settled"]; sum_f += st["sum_frontier"]
                 nsolves += 1
         torch.cuda.synchronize()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
     if pg:
-        t = torch.tensor([total_ms], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        total_ms = float(t.item())
         pg.barrier()
-    value = ws * edges / (total_ms * 1e-3) / 1e9
-    kernel_ms = total_ms / args.steps
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    local_ms = sum(step_ms)
+    local_edges = edges
+    total_ms, tot = combine_ranks(pg, "cuda", local_ms,
+                                  {"edges": edges, "phases": phases, "settled": settled,
+                                   "sum_f": sum_f, "solves": nsolves})
+    value = tot["edges"] / (total_ms * 1e-3) / 1e9
+    kernel_ms = local_ms / args.steps
 
     # roofline of the solve kernel: algorithmic bytes per launch / launch time
     # per solve: 16 B per relaxed edge (8 B edge + 8 B distance word) + 16 B per
     # settled vertex + 16 B per frontier entry per phase
-    alg_bytes = (16 * edges + 16 * settled + 16 * sum_f) / args.steps
+    alg_bytes = (16 * local_edges + 16 * settled + 16 * sum_f) / args.steps
     achieved = alg_bytes / (kernel_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": None, "peak_kind": peak_kind, "kernel": "k_solve_grid" if not batched else "k_solve_batch"}
+                "traffic": None if batched else measured_traffic(wl.name, args.criterion),
+                "peak_kind": peak_kind, "kernel": "k_solve_grid" if not batched else "k_solve_batch"}
 
     # ---- learned per-phase policy (trained here on small graphs, by the
     # library's own FP32 kernels), same workload and timing rules
@@ -279,27 +332,30 @@ def main():
         lcrit = sp.IN_OUT | sp.POLICY_LEARNED
         lstats = []
         for k in range(len(wl.solves)):
-            gi, s = wl.solves[k]
+            gi, s = rank_solve(wl.solves, rank, k)
             _, st, _, _ = sp.solve_trace(Gr[gi], s, lcrit, settle=False)
             lstats.append(st)
         for k in range(args.warmup):
-            gi, s = wl.solves[k % len(wl.solves)]
+            gi, s = rank_solve(wl.solves, rank, k)
             sp.solve(Gr[gi], s, lcrit, out=outs[gi])
         lev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
         ledges = lphases = 0
         torch.cuda.synchronize()
         for k in range(args.steps):
             flush.zero_()
-            gi, s = wl.solves[k % len(wl.solves)]
+            gi, s = rank_solve(wl.solves, rank, k)
             lev[k][0].record(stream)
             sp.solve(Gr[gi], s, lcrit, out=outs[gi])
             lev[k][1].record(stream)
             ledges += lstats[k % len(lstats)]["edges_relaxed"]
             lphases += lstats[k % len(lstats)]["phases"]
         torch.cuda.synchronize()
-        lms = sum(a.elapsed_time(b) for a, b in lev)
-        learned = {"value": ws * ledges / (lms * 1e-3) / 1e9, "unit": "GTEPS", "ms_per_step": lms / args.steps,
-                   "phases_per_solve": lphases / args.steps, "speedup_vs_in_out": total_ms / lms,
+        if pg:
+            pg.barrier()
+        lms_local = sum(a.elapsed_time(b) for a, b in lev)
+        lms, ltot = combine_ranks(pg, "cuda", lms_local, {"edges": ledges})
+        learned = {"value": ltot["edges"] / (lms * 1e-3) / 1e9, "unit": "GTEPS", "ms_per_step": lms / args.steps,
+                   "phases_per_solve": lphases / args.steps, "speedup_vs_in_out": local_ms / lms_local,
                    "train_s": round(train_s, 2), "final_train_loss": hist[-1][1] if hist else None}
         sp.policy_clear()
 
@@ -326,17 +382,20 @@ def main():
             B.launch()
             bev[k][1].record(stream)
         torch.cuda.synchronize()
-        bms = sum(a.elapsed_time(b) for a, b in bev) / args.steps
+        if pg:
+            pg.barrier()
+        bms_local = sum(a.elapsed_time(b) for a, b in bev) / args.steps
+        bms, btot = combine_ranks(pg, "cuda", bms_local, {"edges": bedges, "sources": len(rng_src)})
         batched_leg = {"sources": len(rng_src), "ms_per_launch": bms,
-                       "queries_per_s": ws * len(rng_src) / (bms * 1e-3),
-                       "value": ws * bedges / (bms * 1e-3) / 1e9, "unit": "GTEPS",
-                       "speedup_queries_vs_single": (len(rng_src) / bms) / (nsolves / total_ms)}
+                       "queries_per_s": btot["sources"] / (bms * 1e-3),
+                       "value": btot["edges"] / (bms * 1e-3) / 1e9, "unit": "GTEPS",
+                       "speedup_queries_vs_single": (len(rng_src) / bms_local) / (nsolves / local_ms)}
         B.close()
 
     # ---- end to end through the public API with host buffers
     e2e = None
     if not batched:
-        gi, s = wl.solves[0]
+        gi, s = rank_solve(wl.solves, rank, 0)
         g = wl.graphs[gi]
         pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
         ro, col, w = pin(g.row_off), pin(g.col), pin(g.w)
@@ -353,7 +412,10 @@ def main():
             if r > 0:
                 e2e_t += dt
                 e2e_edges += per_solve[0]["edges_relaxed"]
-        e2e = {"value": ws * e2e_edges / e2e_t / 1e9, "unit": "GTEPS",
+        if pg:
+            pg.barrier()
+        e2e_ms, etot = combine_ranks(pg, "cuda", 1e3 * e2e_t, {"edges": e2e_edges})
+        e2e = {"value": etot["edges"] / (e2e_ms * 1e-3) / 1e9, "unit": "GTEPS",
                "h2d_bytes_per_step": int(ro.nbytes + col.nbytes + w.nbytes),
                "d2h_bytes_per_step": int(dist_h.nbytes + 8), "includes": "graph create (H2D + preprocessing) + solve + D2H"}
 
@@ -367,8 +429,9 @@ def main():
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": wl.name, "criterion": args.criterion, "solves_per_step": nsolves // args.steps,
-                       "phases_per_solve": phases / nsolves, "queries_per_s": ws * nsolves / (total_ms * 1e-3),
-                       "us_per_phase": 1e3 * total_ms / phases, "sum_frontier_per_solve": sum_f / nsolves,
+                       "phases_per_solve": tot["phases"] / tot["solves"],
+                       "queries_per_s": tot["solves"] / (total_ms * 1e-3),
+                       "us_per_phase": 1e3 * local_ms / phases, "sum_frontier_per_solve": tot["sum_f"] / tot["solves"],
                        "prep_ms": prep_ms, "l2": "flushed between steps (2x L2 buffer written)",
                        "parallelism": f"replicas x{ws}"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
