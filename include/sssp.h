@@ -133,10 +133,16 @@ typedef struct {
   uint64_t min_out;        /* OUT threshold used (UINT64_MAX if none) */
   uint64_t deg_settled;    /* sum of out-degrees of S' */
   uint32_t criterion;      /* criterion mask applied in this phase */
-  uint32_t arm;            /* bit 0: dense frontier; bits 8..15: policy arm index */
+  uint32_t arm;            /* bit 0: dense frontier; bit 1: phase ran on one block;
+                              bit 2: near/far split active; bit 3: far part refilled
+                              (or split made) at phase start; bit 7: policy choice,
+                              bits 8..15: its arm index */
   uint64_t t_start_ns;     /* device %globaltimer at phase start */
   uint64_t t_end_ns;       /* device %globaltimer at phase end */
-  uint64_t reserved;
+  uint32_t queued;         /* fringe vertices in the scanned queue (|F| minus the
+                              far part of a near/far split) */
+  uint32_t select_ns;      /* from phase start to the end of the selection step
+                              (the rest of the phase is the relaxation) */
 } sssp_phase_record;
 
 /*
@@ -271,14 +277,24 @@ sssp_status sssp_solve_noalloc(uint32_t n, uint64_t m, const uint64_t* row_offse
  * all blocks of the solve;
  * batch_blocks_per_solve: blocks that cooperate on one solve of a batch (0 =
  * chosen from the batch); grid_blocks: blocks of a single solve (0 = chosen
- * from n, capped at the co-resident maximum).  Applies to launches made after
- * the call; sssp_set_tuning(NULL) restores the defaults (4096, 0, 0, 2048). */
+ * from n, capped at the co-resident maximum);
+ * nearfar_min_frontier: with static criteria only (IN-STATIC and/or
+ * OUT-STATIC, no policy) and n <= 2^30, a fringe of at least this many
+ * vertices is split into a near part, kept in the queue that every phase
+ * scans, and a far part of vertices that no phase can settle before a bound B
+ * on d(v) - inmin(v) is raised (0 = never split);
+ * nearfar_target: vertices the near part is sized to when B is set or raised
+ * (0 = chosen from n and the settled count of the last phase).  Applies to
+ * launches made after the call; sssp_set_tuning(NULL) restores the defaults
+ * (4096, 0, 0, 2048, 65536, 0). */
 typedef struct {
   uint32_t solo_max_frontier;
   uint32_t batch_blocks_per_solve;
   uint32_t grid_blocks;
   uint32_t solo_max_edges;
-  uint32_t reserved[4];
+  uint32_t nearfar_min_frontier;
+  uint32_t nearfar_target;
+  uint32_t reserved[2];
 } sssp_tuning;
 sssp_status sssp_set_tuning(const sssp_tuning* t);
 sssp_status sssp_get_tuning(sssp_tuning* t);

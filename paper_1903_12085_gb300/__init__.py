@@ -40,7 +40,8 @@ STATUS = {0: "SSSP_OK", 1: "SSSP_ERR_INVALID_ARG", 2: "SSSP_ERR_OUT_OF_MEMORY", 
 
 PHASE_RECORD = np.dtype([("frontier", "<u4"), ("settled", "<u4"), ("min_d", "<u8"), ("min_out", "<u8"),
                          ("deg_settled", "<u8"), ("criterion", "<u4"), ("arm", "<u4"),
-                         ("t_start_ns", "<u8"), ("t_end_ns", "<u8"), ("reserved", "<u8")])
+                         ("t_start_ns", "<u8"), ("t_end_ns", "<u8"), ("queued", "<u4"),
+                         ("select_ns", "<u4")])
 assert PHASE_RECORD.itemsize == 64
 
 
@@ -143,25 +144,25 @@ def selftest_wait(limit_ns: int) -> int:
 class Tuning(ctypes.Structure):
     _fields_ = [("solo_max_frontier", ctypes.c_uint32), ("batch_blocks_per_solve", ctypes.c_uint32),
                 ("grid_blocks", ctypes.c_uint32), ("solo_max_edges", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32 * 4)]
+                ("nearfar_min_frontier", ctypes.c_uint32), ("nearfar_target", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 2)]
 
 
-def set_tuning(solo_max_frontier=None, batch_blocks_per_solve=None, grid_blocks=None, solo_max_edges=None):
-    """sssp_set_tuning; unspecified fields keep their current value.
-    set_tuning() with no argument restores the defaults."""
-    if solo_max_frontier is None and batch_blocks_per_solve is None and grid_blocks is None \
-            and solo_max_edges is None:
+def set_tuning(**fields):
+    """sssp_set_tuning; fields not given keep their current value (names as in
+    sssp_tuning: solo_max_frontier, batch_blocks_per_solve, grid_blocks,
+    solo_max_edges, nearfar_min_frontier, nearfar_target).  set_tuning() with
+    no argument restores the defaults."""
+    if not fields:
         _check(lib().sssp_set_tuning(None))
         return
     t = get_tuning()
-    if solo_max_edges is not None:
-        t.solo_max_edges = int(solo_max_edges)
-    if grid_blocks is not None:
-        t.grid_blocks = int(grid_blocks)
-    if solo_max_frontier is not None:
-        t.solo_max_frontier = int(solo_max_frontier)
-    if batch_blocks_per_solve is not None:
-        t.batch_blocks_per_solve = int(batch_blocks_per_solve)
+    names = {f for f, _ in Tuning._fields_ if f != "reserved"}
+    for k, v in fields.items():
+        if k not in names:
+            raise TypeError(f"unknown tuning field {k!r}")
+        if v is not None:
+            setattr(t, k, int(v))
     _check(lib().sssp_set_tuning(ctypes.byref(t)))
 
 

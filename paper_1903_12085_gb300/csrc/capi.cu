@@ -14,12 +14,16 @@ std::atomic<uint32_t> g_solo_max{kSoloMaxDefault};
 std::atomic<uint32_t> g_batch_bpg{0};
 std::atomic<uint32_t> g_grid_blocks{0};
 std::atomic<uint32_t> g_solo_edges{kSoloEdgesDefault};
+std::atomic<uint32_t> g_nf_min{kNearFarMinDefault};
+std::atomic<uint32_t> g_nf_target{0};
 }  // namespace
 
 uint32_t solo_max() { return g_solo_max.load(); }
 uint32_t batch_blocks_per_solve() { return g_batch_bpg.load(); }
 uint32_t grid_blocks() { return g_grid_blocks.load(); }
 uint32_t solo_edges() { return g_solo_edges.load(); }
+uint32_t nearfar_min() { return g_nf_min.load(); }
+uint32_t nearfar_target() { return g_nf_target.load(); }
 
 sssp_status fail(sssp_status st, const char* fmt, ...) {
   va_list ap;
@@ -88,12 +92,16 @@ extern "C" sssp_status sssp_set_tuning(const sssp_tuning* t) {
     sssp::g_batch_bpg.store(0);
     sssp::g_grid_blocks.store(0);
     sssp::g_solo_edges.store(sssp::kSoloEdgesDefault);
+    sssp::g_nf_min.store(sssp::kNearFarMinDefault);
+    sssp::g_nf_target.store(0);
     return SSSP_OK;
   }
   sssp::g_solo_max.store(t->solo_max_frontier);
   sssp::g_batch_bpg.store(t->batch_blocks_per_solve);
   sssp::g_grid_blocks.store(t->grid_blocks);
   sssp::g_solo_edges.store(t->solo_max_edges);
+  sssp::g_nf_min.store(t->nearfar_min_frontier);
+  sssp::g_nf_target.store(t->nearfar_target);
   return SSSP_OK;
 }
 
@@ -104,6 +112,8 @@ extern "C" sssp_status sssp_get_tuning(sssp_tuning* t) {
   t->batch_blocks_per_solve = sssp::g_batch_bpg.load();
   t->grid_blocks = sssp::g_grid_blocks.load();
   t->solo_max_edges = sssp::g_solo_edges.load();
+  t->nearfar_min_frontier = sssp::g_nf_min.load();
+  t->nearfar_target = sssp::g_nf_target.load();
   return SSSP_OK;
 }
 

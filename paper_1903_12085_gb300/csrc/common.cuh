@@ -21,6 +21,15 @@ constexpr uint32_t kInf32 = 0xFFFFFFFFu;
 // of the record tells a relaxation both d and whether the target is settled.
 constexpr uint64_t kUnexplored = 0x7FFFFFFFFFFFFFFFull;
 constexpr uint64_t kSettledBit = 0x8000000000000000ull;
+// Near/far split of the fringe (n <= 2^30, so every distance is < 2^62): a
+// fringe vertex with d(v) - inmin(v) above the bound B is "far" and stores
+// d | kFarBit.  Whether the bit is set is a monotone function of d for a fixed
+// vertex and B, so the stored words keep the order of the distances and
+// atomicMin on them stays exact; every far word is below kUnexplored.
+constexpr uint64_t kFarBit = 0x4000000000000000ull;
+constexpr uint64_t kNoBound = 0x3FFFFFFFFFFFFFFFull;  // B when no vertex is far
+constexpr uint32_t kNearFarMaxVertices = 1u << 30;
+constexpr int kNfBins = 256;  // key histogram: 4 bins per octave
 
 // Vertex status: unexplored, fringe (queued), settled (Section 2's U, F, S).
 enum : uint8_t { kU = 0, kF = 1, kS = 2 };
@@ -81,6 +90,9 @@ struct PhaseSlot {
   unsigned int settled_now;       // |S'| of this phase
   unsigned int arm;               // arm the phase ran with (policy index << 8 | dense)
   unsigned long long t_start;     // %globaltimer when the phase began (trace)
+  unsigned int fsize;             // |F| at the start of the phase (queue + far part)
+  unsigned int pad;
+  unsigned long long t_select;    // %globaltimer when the selection step ended (trace)
 };
 
 // Per-solve control block in device memory (zeroed before each launch).
@@ -94,6 +106,11 @@ struct Ctl {
   unsigned int resume_relax;     // solo mode: 1 = the group resumes at the relax step of next_phase
   unsigned int pad;
   GridBarrier bar;
+  // near/far split: far fringe vertices, a work counter and two key
+  // histograms (use u fills hist[u & 1] while the other one is cleared)
+  unsigned int far_count;
+  unsigned int nf_tmp;
+  unsigned int hist[2][kNfBins];
 };
 
 // Mutable per-solve buffers.

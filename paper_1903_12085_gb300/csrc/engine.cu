@@ -153,9 +153,13 @@ struct Mode {
   bool use_out;
   bool out_dyn;      // OUT-SIMPLE (three-step kind)
   bool dijk;
+  bool nearfar;      // the fringe may be split into a near queue and a far part
 };
 
-__device__ __forceinline__ Mode mode_of(uint32_t crit, bool has_cur_in) {
+// The near/far split needs static keys d(v) - inmin(v) (no IN-SIMPLE phase, so
+// no policy either) and fused thresholds, and n <= 2^30 for the far bit.
+__device__ __forceinline__ Mode mode_of(const SolveParams& p) {
+  const uint32_t crit = p.crit;
   Mode m;
   m.out_dyn = (crit & SSSP_OUT_SIMPLE) != 0;
   m.use_out = m.out_dyn || (crit & SSSP_OUT_STATIC) != 0;
@@ -163,7 +167,7 @@ __device__ __forceinline__ Mode mode_of(uint32_t crit, bool has_cur_in) {
   m.fused = !m.out_dyn && !m.dijk;
   const bool policy = (crit & SSSP_POLICY_LEARNED) != 0;
   m.use_in = (crit & (SSSP_IN_STATIC | SSSP_IN_SIMPLE)) != 0 || policy;
-  (void)has_cur_in;
+  m.nearfar = m.fused && !policy && !(crit & SSSP_IN_SIMPLE) && p.nf_min != 0 && p.g.n <= kNearFarMaxVertices;
   return m;
 }
 
@@ -204,6 +208,10 @@ __device__ Arm choose_arm(const SolveParams& p, uint64_t k, uint32_t nF, uint64_
   return a;
 }
 
+// Trace arm bits of the near/far split: split active in the phase; the far
+// part was refilled (or the split made) at the start of the phase.
+constexpr uint32_t kArmNfActive = 4u, kArmNfRefill = 8u;
+
 __device__ __forceinline__ uint32_t arm_code(const Arm& a, bool solo) {
   return (a.dense ? 1u : 0u) | (solo ? 2u : 0u) | (a.index >= 0 ? ((uint32_t)a.index << 8) | 0x80u : 0u);
 }
@@ -215,6 +223,7 @@ __device__ __forceinline__ void reset_slot(PhaseSlot* s) {
   s->argmin = kInf32;
   s->settled_now = 0;
   s->arm = 0;
+  s->fsize = 0;
 }
 
 // Relaxation of one edge (u -> t) with d[u] = du (step C, any mode): one
@@ -225,25 +234,42 @@ __device__ __forceinline__ void reset_slot(PhaseSlot* s) {
 // below the value read before the update contributes to the next phase's fused
 // thresholds: the final d[t] is always contributed by the relaxation that
 // wrote it, and every contribution is >= the final d[t].
+// Near/far split (bound < kNoBound): the candidate is stored with kFarBit when
+// its key du + c - inmin(t) exceeds the bound.  A new vertex that is far is
+// only counted (dfar); a far vertex whose stored word loses the bit is moved
+// to the near queue by the one relaxation whose atomicMin saw the bit go.
+// `fresh` asks the caller to append t to the next queue.
 __device__ __forceinline__ void relax_edge(const SolveParams& p, const Mode& md, uint32_t t, uint32_t cost,
-                                           unsigned long long du, unsigned long long& pd, unsigned long long& po,
-                                           bool& fresh) {
+                                           unsigned long long du, unsigned long long bound,
+                                           unsigned long long& pd, unsigned long long& po, bool& fresh, int& dfar) {
   const SolveWS& w = p.ws;
   const VRec rt = ldcg_vrec(&w.vrec[t]);
   if (rt.d & kSettledBit) return;
   const unsigned long long cand = du + cost;
-  if (cand < rt.d) {
+  unsigned long long enc = cand;
+  if (md.nearfar && cand > bound + rt.im) enc |= kFarBit;
+  if (enc < rt.d) {
     unsigned long long old = rt.d;
     if (rt.d == kUnexplored) {
-      old = atomicMin(&w.vrec[t].d, cand);
+      old = atomicMin(&w.vrec[t].d, enc);
       if (old == kUnexplored) {
         w.status[t] = kF;
+        if (enc & kFarBit) ++dfar;
+        else fresh = true;
+      } else if (md.nearfar && (old & kFarBit) && !(enc & kFarBit)) {
+        fresh = true;  // old < kUnexplored: t was far and is near now
+        --dfar;
+      }
+    } else if (md.nearfar && (rt.d & kFarBit) && !(enc & kFarBit)) {
+      old = atomicMin(&w.vrec[t].d, enc);
+      if (old & kFarBit) {  // old <= rt.d < kUnexplored
         fresh = true;
+        --dfar;
       }
     } else {
-      red_min_u64(&w.vrec[t].d, cand);
+      red_min_u64(&w.vrec[t].d, enc);
     }
-    if (md.fused && cand < old) {
+    if (md.fused && enc < old) {
       pd = cand < pd ? cand : pd;
       if (rt.om != kInf32) {
         const unsigned long long x = cand + rt.om;
@@ -277,7 +303,9 @@ __device__ bool phase_select(const SolveParams& p, const Grp& grp, const Mode& m
   const bool in_dyn = md.use_in && arm.in_simple && w.cur_in != nullptr;
   if (leader) {
     reset_slot(&ctl->slot[(k + 2) % 4]);
-    st.sum_f += nF;
+    const uint32_t fs = nF + (md.nearfar ? ldcg_u32(&ctl->far_count) : 0u);
+    S0->fsize = fs;
+    st.sum_f += fs;
     if (w.trace) S0->t_start = globaltimer_ns();
   }
 
@@ -372,6 +400,11 @@ __device__ bool phase_select(const SolveParams& p, const Grp& grp, const Mode& m
 #pragma unroll
     for (int j = 0; j < kSelItems; ++j)
       if (ok[j]) rr[j] = ldcg_vrec(&w.vrec[vv[j]]);
+    if (dense && md.nearfar) {  // a dense scan also meets the far part of F
+#pragma unroll
+      for (int j = 0; j < kSelItems; ++j)
+        if (ok[j] && (rr[j].d & kFarBit)) ok[j] = false;
+    }
     uint32_t selm = 0, keepm = 0;
     uint2 rd[kSelItems];
 #pragma unroll
@@ -453,7 +486,7 @@ __device__ bool phase_select(const SolveParams& p, const Grp& grp, const Mode& m
 // the end-of-phase barrier, counters and trace.  Every block of the group
 // calls it.  Returns false if a barrier gave up.
 __device__ bool phase_relax(const SolveParams& p, const Grp& grp, const Mode& md, const Arm arm, uint64_t k,
-                            const Shared& sh, Stats& st) {
+                            unsigned long long bound, bool resumed, const Shared& sh, Stats& st) {
   const GraphView& g = p.g;
   const SolveWS& w = p.ws;
   Ctl* ctl = w.ctl;
@@ -466,9 +499,11 @@ __device__ bool phase_relax(const SolveParams& p, const Grp& grp, const Mode& md
   PhaseSlot* S0 = &ctl->slot[k % 4];
   PhaseSlot* S1 = &ctl->slot[(k + 1) % 4];
   unsigned long long pd = kInf64, po = kInf64;
+  int dfar = 0;
   const unsigned long long packed = ldcg_u64(&S0->relax_packed);
   const uint32_t nS = (uint32_t)(packed >> 32);
   const uint32_t E = (uint32_t)packed;
+  if (leader && w.trace && !resumed) S0->t_select = globaltimer_ns();  // (a hand-off set it)
   for (uint64_t tile = grp.rank; tile * kTile < E; tile += grp.size) {
     const uint32_t e0 = (uint32_t)(tile * kTile);
     const uint32_t e1 = (uint64_t)e0 + kTile < E ? e0 + kTile : E;
@@ -503,7 +538,7 @@ __device__ bool phase_relax(const SolveParams& p, const Grp& grp, const Mode& md
         }
         const uint2 ed = __ldg(&g.edges[sh.s_row[a] + (e - sh.s_base[a])]);
         bool fresh = false;
-        relax_edge(p, md, ed.x, ed.y, sh.s_d[a], pd, po, fresh);
+        relax_edge(p, md, ed.x, ed.y, sh.s_d[a], bound, pd, po, fresh, dfar);
         if (fresh) {
           fv[it] = ed.x;
           fmask |= 1u << it;
@@ -526,6 +561,11 @@ __device__ bool phase_relax(const SolveParams& p, const Grp& grp, const Mode& md
     __syncthreads();
   }
   if (md.fused) block_min2_to_global(pd, po, &S1->min_d, md.use_out ? &S1->min_out : nullptr, sh.red);
+  if (md.nearfar) {  // far-part count: one atomic per block (the barrier above orders scratch reuse)
+    uint32_t tf;
+    block_exclusive_scan((uint32_t)dfar, sh.scan, &tf);
+    if (tid == 0 && tf) atomicAdd(&ctl->far_count, tf);
+  }
   if (!grp.sync()) return false;
   if (leader) {
     const uint32_t settled_now = ldcg_u32(&S0->settled_now);
@@ -537,7 +577,7 @@ __device__ bool phase_relax(const SolveParams& p, const Grp& grp, const Mode& md
       const bool in_dyn = md.use_in && w.cur_in != nullptr &&
                           ((code & 0x80u) ? ((code >> 8) >= 2) : arm.in_simple);
       sssp_phase_record r;
-      r.frontier = ldcg_u32(&S0->qcount);
+      r.frontier = ldcg_u32(&S0->fsize);
       r.settled = settled_now;
       r.min_d = md.fused ? ldcg_u64(&S0->min_d) : ldcg_u64(&S0->a_min_d);
       r.min_out = md.use_out ? (md.fused ? ldcg_u64(&S0->min_out) : ldcg_u64(&S0->a_min_out)) : kInf64;
@@ -548,7 +588,8 @@ __device__ bool phase_relax(const SolveParams& p, const Grp& grp, const Mode& md
       r.arm = ldcg_u32(&S0->arm);
       r.t_start_ns = ldcg_u64(&S0->t_start);
       r.t_end_ns = globaltimer_ns();
-      r.reserved = 0;
+      r.queued = ldcg_u32(&S0->qcount);
+      r.select_ns = (uint32_t)(ldcg_u64(&S0->t_select) - r.t_start_ns);
       w.trace[k - 1] = r;
     }
   }
@@ -556,14 +597,14 @@ __device__ bool phase_relax(const SolveParams& p, const Grp& grp, const Mode& md
 }
 
 __device__ __forceinline__ bool run_phase(const SolveParams& p, const Grp& grp, const Mode& md, uint64_t k,
-                                          const Shared& sh, Stats& st) {
+                                          unsigned long long bound, uint32_t nf_code, const Shared& sh, Stats& st) {
   const PhaseSlot* prev = &p.ws.ctl->slot[(k + 3) % 4];
   const Arm arm = choose_arm(p, k, ldcg_u32(&p.ws.ctl->slot[k % 4].qcount),
                              (uint32_t)ldcg_u64(&prev->relax_packed), ldcg_u32(&prev->settled_now),
                              ldcg_u32(&prev->qcount));
-  if (grp.rank == 0 && threadIdx.x == 0) p.ws.ctl->slot[k % 4].arm = arm_code(arm, grp.size == 1);
+  if (grp.rank == 0 && threadIdx.x == 0) p.ws.ctl->slot[k % 4].arm = arm_code(arm, grp.size == 1) | nf_code;
   if (!phase_select(p, grp, md, arm, k, sh, st)) return false;
-  return phase_relax(p, grp, md, arm, k, sh, st);
+  return phase_relax(p, grp, md, arm, k, bound, false, sh, st);
 }
 
 // Solo episode (fused thresholds only): this block runs phases k, k+1, ...
@@ -578,8 +619,8 @@ __device__ __forceinline__ bool run_phase(const SolveParams& p, const Grp& grp, 
 // slot[k%3].  Exit at phase k: the same state with slot[(k+1)%3] reset (no
 // handoff), or the state after a grid selection step of phase k (handoff).
 // All threads of the block call it.
-__device__ uint64_t solo_episode(const SolveParams& p, const Mode& md, uint64_t k, unsigned char* smem, Stats& st,
-                                 bool can_handoff, bool* handoff) {
+__device__ uint64_t solo_episode(const SolveParams& p, const Mode& md, uint64_t k, unsigned long long bound,
+                                 uint32_t nf_code, unsigned char* smem, Stats& st, bool can_handoff, bool* handoff) {
   const GraphView& g = p.g;
   const SolveWS& w = p.ws;
   Ctl* ctl = w.ctl;
@@ -599,6 +640,7 @@ __device__ uint64_t solo_episode(const SolveParams& p, const Mode& md, uint64_t 
   __shared__ unsigned int s_qn, s_settled;
   __shared__ unsigned int s_wk[32], s_wr[32], s_we[32];  // per-warp counts, then offsets
   __shared__ unsigned long long s_relax, s_thr_d, s_thr_o;
+  __shared__ int s_dfar;
   *handoff = false;
 
   const uint32_t cap = p.solo_max < kSoloCap ? p.solo_max : kSoloCap;
@@ -607,6 +649,7 @@ __device__ uint64_t solo_episode(const SolveParams& p, const Mode& md, uint64_t 
   uint64_t s_prev = ldcg_u32(&ctl->slot[(k + 3) % 4].settled_now);
   uint64_t f_prev = ldcg_u32(&ctl->slot[(k + 3) % 4].qcount);
   uint32_t nF = ldcg_u32(&ctl->slot[k % 4].qcount);
+  uint32_t far = md.nearfar ? ldcg_u32(&ctl->far_count) : 0u;  // far part of F (not in the queues)
   Arm arm{false, false, -1};
   unsigned int since_pick = 0;
   unsigned long long minD = ldcg_u64(&ctl->slot[k % 4].min_d);
@@ -626,13 +669,15 @@ __device__ uint64_t solo_episode(const SolveParams& p, const Mode& md, uint64_t 
     if (since_pick == 0) arm = choose_arm(p, k, nF, e_prev, s_prev, f_prev);
     since_pick = (since_pick + 1) & 3u;
     const bool in_dyn = md.use_in && arm.in_simple && w.cur_in != nullptr;
-    unsigned long long t0 = 0;
+    const uint32_t fs = nF + far;  // |F| at the start of the phase
+    unsigned long long t0 = 0, t_sel = 0;
     if (tid == 0) {
       t0 = globaltimer_ns();
       s_qn = 0;
       s_settled = 0;
       s_relax = 0;
       s_thr_d = s_thr_o = kInf64;
+      s_dfar = 0;
     }
     // ---- B1: stage the fringe's records (all of a thread's loads in flight at once)
     for (uint32_t i0 = tid; i0 < nF; i0 += 4 * nthr) {
@@ -776,18 +821,22 @@ __device__ uint64_t solo_episode(const SolveParams& p, const Mode& md, uint64_t 
       const uint32_t nk = kept < kSoloCap ? kept : kSoloCap;
       for (uint32_t j = tid; j < nk; j += nthr) gqn[j] = sqn[j];
       if (tid == 0) {
-        st.sum_f += nF;
+        st.sum_f += fs;
+        ctl->far_count = far;
         PhaseSlot* S0 = &ctl->slot[k % 4];
         PhaseSlot* S1 = &ctl->slot[(k + 1) % 4];
         reset_slot(S0);
         reset_slot(S1);
         reset_slot(&ctl->slot[(k + 2) % 4]);
         S0->qcount = nF;
+        S0->fsize = fs;
         S0->min_d = minD;
         S0->min_out = minOut;
         S0->relax_packed = packed;
         S0->settled_now = s_settled;
-        S0->arm = arm_code(arm, true);
+        S0->arm = arm_code(arm, true) | nf_code;
+        S0->t_start = t0;
+        S0->t_select = globaltimer_ns();
         S1->qcount = kept;
         S1->min_d = s_thr_d;
         S1->min_out = s_thr_o;
@@ -798,8 +847,10 @@ __device__ uint64_t solo_episode(const SolveParams& p, const Mode& md, uint64_t 
       return k;
     }
     // ---- C: relax
+    if (tid == 0) t_sel = globaltimer_ns();
     pd = kInf64;
     po = kInf64;
+    int dfar = 0;
     for (uint32_t eb = warp * 32; eb < E; eb += nthr) {
       const uint32_t e = eb + lane;
       bool fresh = false;
@@ -812,7 +863,7 @@ __device__ uint64_t solo_episode(const SolveParams& p, const Mode& md, uint64_t 
         }
         const uint2 ed = __ldg(&g.edges[sp_row[a] + (e - sp_base[a])]);
         t = ed.x;
-        relax_edge(p, md, t, ed.y, sp_d[a], pd, po, fresh);
+        relax_edge(p, md, t, ed.y, sp_d[a], bound, pd, po, fresh, dfar);
       }
       const unsigned int fmask = __ballot_sync(0xFFFFFFFFu, fresh);
       if (fmask) {
@@ -829,21 +880,23 @@ __device__ uint64_t solo_episode(const SolveParams& p, const Mode& md, uint64_t 
     }
     pd = warp_min_u64(pd);
     po = warp_min_u64(po);
+    if (md.nearfar) dfar = __reduce_add_sync(0xFFFFFFFFu, dfar);
     if (lane == 0) {
       if (pd != kInf64) atomicMin(&s_thr_d, pd);
       if (po != kInf64 && md.use_out) atomicMin(&s_thr_o, po);
+      if (dfar) atomicAdd(&s_dfar, dfar);
     }
     __syncthreads();
     const uint32_t nFn = s_qn;
     if (tid == 0) {
       st.phases = k;
-      st.sum_f += nF;
+      st.sum_f += fs;
       st.settled += s_settled;
       st.relaxed += E;
       ctl->heartbeat = k;
       if (w.trace && k <= w.trace_cap) {
         sssp_phase_record r;
-        r.frontier = nF;
+        r.frontier = fs;
         r.settled = s_settled;
         r.min_d = minD;
         r.min_out = md.use_out ? minOut : kInf64;
@@ -851,22 +904,27 @@ __device__ uint64_t solo_episode(const SolveParams& p, const Mode& md, uint64_t 
         uint32_t c = p.crit & SSSP_CRITERIA_MASK;
         if (md.use_in) c = (c & ~(uint32_t)(SSSP_IN_STATIC | SSSP_IN_SIMPLE)) | (in_dyn ? SSSP_IN_SIMPLE : SSSP_IN_STATIC);
         r.criterion = c;
-        r.arm = arm_code(arm, true);
+        r.arm = arm_code(arm, true) | nf_code;
         r.t_start_ns = t0;
         r.t_end_ns = globaltimer_ns();
-        r.reserved = 0;
+        r.queued = nF;
+        r.select_ns = (uint32_t)(t_sel - t0);
         w.trace[k - 1] = r;
       }
     }
+    nf_code &= ~kArmNfRefill;  // a refill or split only runs before the episode
     minD = s_thr_d;
     minOut = s_thr_o;
     e_prev = E;
     s_prev = s_settled;
     f_prev = nF;
     nF = nFn;
+    far += (uint32_t)s_dfar;
     ++k;
     __syncthreads();  // shared counters are read before the next phase resets them
-    if (nF == 0 || nF > cap) break;
+    if (nF == 0 || nF > cap || k > (uint64_t)n + 1) break;
+    // thresholds above the bound are exact only after the far part is scanned
+    if (far > 0 && (md.use_out ? minOut : minD) > bound) break;
   }
   // hand the state back in global memory for phase k
   {
@@ -879,6 +937,7 @@ __device__ uint64_t solo_episode(const SolveParams& p, const Mode& md, uint64_t 
     PhaseSlot* S0 = &ctl->slot[k % 4];
     reset_slot(S0);
     reset_slot(&ctl->slot[(k + 1) % 4]);
+    ctl->far_count = far;
     S0->qcount = nF;
     S0->min_d = minD;
     S0->min_out = minOut;
@@ -890,6 +949,293 @@ __device__ uint64_t solo_episode(const SolveParams& p, const Mode& md, uint64_t 
   __threadfence();
   __syncthreads();
   return k;
+}
+
+// ---------------------------------------------------------------------------
+// Near/far split of the fringe (static criteria).  key(v) = d(v) - inmin(v).
+// Invariant: a fringe vertex is far (kFarBit set, not in the queue) iff
+// key(v) > B; the queue holds exactly the near fringe.  A vertex that any
+// criterion settles has key(v) <= T, where T = minOut with an OUT criterion,
+// else minD (IN: key <= minD; OUT: key <= d <= minOut; minD <= minOut).  A far
+// vertex has d >= key > B, so whenever the thresholds accumulated over the near
+// part and the relaxations satisfy T <= B they are the thresholds of the whole
+// fringe and every vertex the phase settles is in the queue.  When T > B (and
+// the far part is not empty) a refill first computes the exact minima over the
+// far part and raises B to at least T.  The selections, and so every result,
+// are those of the unsplit fringe.
+
+// Histogram bin of x >= 0: bins 0..3 hold x itself, then 4 bins per octave.
+__device__ __forceinline__ int nf_bin(unsigned long long x) {
+  if (x < 4) return (int)x;
+  const int m = 63 - __clzll((long long)x);
+  return 4 * (m - 1) + (int)((x >> (m - 2)) & 3u);
+}
+
+// Largest x of bin b (saturated at kNoBound).
+__device__ __forceinline__ unsigned long long nf_bin_upper(int b) {
+  if (b < 4) return (unsigned long long)b;
+  const int m = b / 4 + 1, s = b & 3;
+  if (m >= 61) return kNoBound;
+  return (1ull << m) + ((unsigned long long)(s + 1) << (m - 2)) - 1;
+}
+
+__device__ __forceinline__ unsigned long long nf_key(const VRec& r, unsigned long long d) {
+  return (r.im == kInf32 || d <= r.im) ? 0ull : d - r.im;
+}
+
+// Near-part size to aim at when the bound is set: the tuning's value, else
+// about sqrt(n * settled per phase), which balances the per-phase scan of the
+// near queue against the dense refill pass; never more than 1/8 of the fringe,
+// so that the bound lands well inside the fringe's keys.
+__device__ __forceinline__ uint32_t nf_target(const SolveParams& p, uint64_t k, uint32_t fringe) {
+  uint32_t t = p.nf_target;
+  if (t == 0) {
+    const uint32_t s_prev = ldcg_u32(&p.ws.ctl->slot[(k + 3) % 4].settled_now);
+    const float s = (float)(s_prev > 256u ? s_prev : 256u);
+    const float x = 2.0f * sqrtf((float)p.g.n * s);
+    t = x < 4096.0f ? 4096u : (x > (float)p.g.n ? p.g.n : (uint32_t)x);
+  }
+  const uint32_t cap = fringe / 8 > 0 ? fringe / 8 : 1u;
+  return t < cap ? t : cap;
+}
+
+// Adds one to bin `bin` (>= 0) of a shared histogram for every lane that has
+// one; lanes with bin < 0 add nothing.  Lanes with the same bin are counted by
+// one atomic (keys crowd into few bins).  All 32 lanes of the warp call it.
+__device__ __forceinline__ void nf_hist_add(uint32_t* sh_hist, int bin) {
+  const unsigned int peers = __match_any_sync(0xFFFFFFFFu, bin);
+  if (bin >= 0 && (threadIdx.x & 31) == (unsigned)(__ffs(peers) - 1)) atomicAdd(&sh_hist[bin], (uint32_t)__popc(peers));
+}
+
+// Block-local histogram in shared memory, flushed to the group's histogram.
+__device__ __forceinline__ void nf_hist_clear(uint32_t* sh_hist) {
+  for (int b = threadIdx.x; b < kNfBins; b += blockDim.x) sh_hist[b] = 0;
+  __syncthreads();
+}
+__device__ __forceinline__ void nf_hist_flush(const uint32_t* sh_hist, unsigned int* gh) {
+  __syncthreads();
+  for (int b = threadIdx.x; b < kNfBins; b += blockDim.x)
+    if (sh_hist[b]) atomicAdd(&gh[b], sh_hist[b]);
+}
+
+// Smallest bin whose cumulative count reaches `target` (kNfBins if none),
+// read from the group's histogram after a barrier.  Every block computes the
+// same answer.  All threads of the block call it.
+__device__ __forceinline__ int nf_pick_bin(const unsigned int* gh, uint32_t target, const Shared& sh) {
+  __shared__ int s_bin;
+  const uint32_t v = threadIdx.x < kNfBins ? ldcg_u32(&gh[threadIdx.x]) : 0u;
+  if (threadIdx.x == 0) s_bin = kNfBins;
+  uint32_t total;
+  const uint32_t excl = block_exclusive_scan(v, sh.scan, &total);
+  if (threadIdx.x < kNfBins && excl < target && excl + v >= target) s_bin = (int)threadIdx.x;
+  __syncthreads();
+  const int b = s_bin;
+  __syncthreads();
+  return b;
+}
+
+// First split (B = kNoBound, no far vertex, so the phase-k thresholds are
+// exact): B = T + the key offset below which about `target` queue entries lie;
+// entries above B are marked far and the queue is compacted.  Leaves B as is
+// when the whole fringe fits the target.  Every block of the group calls it.
+__device__ __noinline__ bool nf_split(const SolveParams& p, const Grp& grp, const Mode& md, uint64_t k, const Shared& sh,
+                         unsigned long long& bound, uint32_t& uses) {
+  const SolveWS& w = p.ws;
+  Ctl* ctl = w.ctl;
+  const unsigned int tid = threadIdx.x, nthr = blockDim.x;
+  const uint64_t gthreads = (uint64_t)grp.size * nthr;
+  const uint64_t gtid = (uint64_t)grp.rank * nthr + tid;
+  const bool leader = grp.rank == 0 && tid == 0;
+  PhaseSlot* S0 = &ctl->slot[k % 4];
+  uint32_t* Q = w.q[(k - 1) & 1];
+  const uint32_t nF = ldcg_u32(&S0->qcount);
+  const unsigned long long T = md.use_out ? ldcg_u64(&S0->min_out) : ldcg_u64(&S0->min_d);
+  if (T >= kNoBound) return true;
+  unsigned int* gh = ctl->hist[uses & 1];
+  uint32_t* hist = sh.s_base;
+  nf_hist_clear(hist);
+  for (uint64_t c0 = (uint64_t)grp.rank * nthr; c0 < nF; c0 += gthreads) {  // warp-uniform trips
+    const uint64_t i = c0 + tid;
+    int bin = -1;
+    if (i < nF) {
+      const VRec r = ldcg_vrec(&w.vrec[ldcg_u32(&Q[i])]);
+      const unsigned long long key = nf_key(r, r.d);
+      bin = nf_bin(key > T ? key - T : 0ull);
+    }
+    nf_hist_add(hist, bin);
+  }
+  nf_hist_flush(hist, gh);
+  if (leader) ctl->nf_tmp = 0;
+  if (tid < kNfBins && grp.rank == 0) ctl->hist[(uses + 1) & 1][tid] = 0;  // the next use's histogram
+  ++uses;
+  if (!grp.sync()) return false;
+  const int b = nf_pick_bin(gh, nf_target(p, k, nF), sh);
+  if (b >= kNfBins) return true;
+  const unsigned long long e = nf_bin_upper(b);
+  const unsigned long long B = e >= kNoBound - T ? kNoBound : T + e;
+  if (B >= kNoBound) return true;
+  // keep the entries with key <= B (compacted into the relax-list buffer),
+  // mark the others far
+  uint32_t* tmp = reinterpret_cast<uint32_t*>(w.sp);
+  uint32_t demoted = 0;
+  for (uint64_t c0 = (uint64_t)grp.rank * nthr; c0 < nF; c0 += gthreads) {
+    const uint64_t i = c0 + tid;
+    bool keep = false;
+    uint32_t v = 0;
+    if (i < nF) {
+      v = ldcg_u32(&Q[i]);
+      const VRec r = ldcg_vrec(&w.vrec[v]);
+      keep = nf_key(r, r.d) <= B;
+      if (!keep) {
+        w.vrec[v].d = r.d | kFarBit;
+        ++demoted;
+      }
+    }
+    uint32_t tk;
+    const uint32_t pk = block_exclusive_scan(keep ? 1u : 0u, sh.scan, &tk);
+    if (tid == 0) sh.bases[0] = tk ? atomicAdd(&ctl->nf_tmp, tk) : 0u;
+    __syncthreads();
+    if (keep) tmp[(uint32_t)sh.bases[0] + pk] = v;
+    __syncthreads();
+  }
+  uint32_t td;
+  block_exclusive_scan(demoted, sh.scan, &td);
+  if (tid == 0 && td) atomicAdd(&ctl->far_count, td);
+  if (!grp.sync()) return false;
+  const uint32_t kept = ldcg_u32(&ctl->nf_tmp);
+  for (uint64_t i = gtid; i < kept; i += gthreads) Q[i] = ldcg_u32(&tmp[i]);
+  if (leader) S0->qcount = kept;
+  bound = B;
+  return grp.sync();
+}
+
+// Refill (far part not empty, accumulated T > B).  R1: every block scans its
+// own contiguous range of vertex records (kNfItems loads in flight per
+// thread, no block barrier inside the loop), takes the exact minima of d and
+// d + outmin over the far vertices and a histogram of their keys above B, and
+// writes each far vertex as {d, v, inmin} into its own range of the relax-list
+// buffer.  After a group barrier, B' = max(T, B + the offset below which about
+// `target` far vertices lie).  R2: every block reads back only its own far
+// entries and moves those with key <= B' to the queue of phase k.  Every block
+// of the group calls it.
+constexpr int kNfItems = 8;
+
+__device__ __noinline__ bool nf_refill(const SolveParams& p, const Grp& grp, const Mode& md, uint64_t k, const Shared& sh,
+                                       unsigned long long& bound, uint32_t& uses) {
+  const GraphView& g = p.g;
+  const SolveWS& w = p.ws;
+  Ctl* ctl = w.ctl;
+  const uint32_t n = g.n;
+  const unsigned int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31;
+  const bool leader = grp.rank == 0 && tid == 0;
+  PhaseSlot* S0 = &ctl->slot[k % 4];
+  uint32_t* Q = w.q[(k - 1) & 1];
+  unsigned int* gh = ctl->hist[uses & 1];
+  uint32_t* hist = sh.s_base;
+  ulonglong2* tmp = reinterpret_cast<ulonglong2*>(w.sp);
+  __shared__ unsigned int s_fcnt;
+  // this block's vertex range [lo, hi)
+  const uint64_t per = ((uint64_t)n + grp.size - 1) / grp.size;
+  const uint64_t lo = (uint64_t)grp.rank * per;
+  const uint64_t hi = lo + per < n ? lo + per : n;
+  if (tid == 0) s_fcnt = 0;
+  nf_hist_clear(hist);  // (its barrier also publishes s_fcnt)
+  unsigned long long lmin_d = kInf64, lmin_o = kInf64;
+  const uint64_t chunk = (uint64_t)nthr * kNfItems;
+  for (uint64_t c0 = lo; c0 < hi; c0 += chunk) {
+    VRec rr[kNfItems];
+#pragma unroll
+    for (int j = 0; j < kNfItems; ++j) {
+      const uint64_t v = c0 + (uint64_t)j * nthr + tid;
+      rr[j].d = kUnexplored;
+      if (v < hi) rr[j] = ldcg_vrec(&w.vrec[v]);
+    }
+#pragma unroll
+    for (int j = 0; j < kNfItems; ++j) {
+      const bool far = rr[j].d != kUnexplored && (rr[j].d >> 62) == 1u;  // bit 62 set, bit 63 clear
+      const unsigned long long d = rr[j].d & ~kFarBit;
+      int bin = -1;
+      if (far) {
+        lmin_d = d < lmin_d ? d : lmin_d;
+        if (rr[j].om != kInf32) {
+          const unsigned long long x = d + rr[j].om;
+          lmin_o = x < lmin_o ? x : lmin_o;
+        }
+        bin = nf_bin(nf_key(rr[j], d) - bound);
+      }
+      nf_hist_add(hist, bin);
+      const unsigned int fm = __ballot_sync(0xFFFFFFFFu, far);
+      if (fm) {
+        unsigned int base = 0;
+        if (lane == 0) base = atomicAdd(&s_fcnt, (unsigned int)__popc(fm));
+        base = __shfl_sync(0xFFFFFFFFu, base, 0);
+        if (far) {
+          const uint32_t v = (uint32_t)(c0 + (uint64_t)j * nthr + tid);
+          tmp[lo + base + __popc(fm & ((1u << lane) - 1u))] =
+              make_ulonglong2(d, (unsigned long long)v | ((unsigned long long)rr[j].im << 32));
+        }
+      }
+    }
+  }
+  block_min2_to_global(lmin_d, lmin_o, &S0->a_min_d, md.use_out ? &S0->a_min_out : nullptr, sh.red);
+  const uint32_t cnt = s_fcnt;  // this block's far entries (the barrier above published it)
+  nf_hist_flush(hist, gh);
+  if (tid < kNfBins && grp.rank == 0) ctl->hist[(uses + 1) & 1][tid] = 0;
+  ++uses;
+  if (!grp.sync()) return false;
+  const unsigned long long a_d = ldcg_u64(&S0->min_d), f_d = ldcg_u64(&S0->a_min_d);
+  const unsigned long long a_o = ldcg_u64(&S0->min_out), f_o = ldcg_u64(&S0->a_min_out);
+  const unsigned long long minD = a_d < f_d ? a_d : f_d;
+  const unsigned long long minOut = a_o < f_o ? a_o : f_o;
+  const unsigned long long T = md.use_out ? minOut : minD;
+  const int b = nf_pick_bin(gh, nf_target(p, k, ldcg_u32(&S0->qcount) + ldcg_u32(&ctl->far_count)), sh);
+  const unsigned long long e = b >= kNfBins ? kNoBound : nf_bin_upper(b);
+  unsigned long long B = e >= kNoBound - bound ? kNoBound : bound + e;
+  if (B < T) B = T >= kNoBound ? kNoBound : T;
+  uint32_t moved = 0;
+  const uint32_t rchunk = nthr * kSelItems;
+  for (uint32_t c0 = 0; c0 < cnt; c0 += rchunk) {
+    uint32_t mv = 0;
+    uint32_t vv[kSelItems];
+#pragma unroll
+    for (int j = 0; j < kSelItems; ++j) {
+      const uint32_t i = c0 + j * nthr + tid;
+      vv[j] = 0;
+      if (i < cnt) {
+        const ulonglong2 t = __ldcg(&tmp[lo + i]);
+        const uint32_t im = (uint32_t)(t.y >> 32);
+        const unsigned long long key = (im == kInf32 || t.x <= im) ? 0ull : t.x - im;
+        if (key <= B) {
+          vv[j] = (uint32_t)t.y;
+          w.vrec[vv[j]].d = t.x;
+          mv |= 1u << j;
+        }
+      }
+    }
+    uint32_t tm;
+    const uint32_t pm = block_exclusive_scan(__popc(mv), sh.scan, &tm);
+    if (tid == 0) sh.bases[0] = tm ? atomicAdd(&S0->qcount, tm) : 0u;
+    __syncthreads();
+    uint32_t slot = (uint32_t)sh.bases[0] + pm;
+#pragma unroll
+    for (int j = 0; j < kSelItems; ++j)
+      if ((mv >> j) & 1u) {
+        if (slot < n) Q[slot] = vv[j];
+        else atomicCAS(&ctl->err, 0, (int)SSSP_ERR_INTERNAL);
+        ++slot;
+      }
+    moved += __popc(mv);
+    __syncthreads();
+  }
+  uint32_t tm;
+  block_exclusive_scan(moved, sh.scan, &tm);
+  if (tid == 0 && tm) atomicSub(&ctl->far_count, tm);
+  if (leader) {  // the exact thresholds of the whole fringe (idempotent with what every block read)
+    S0->min_d = minD;
+    S0->min_out = minOut;
+  }
+  bound = B;
+  return grp.sync();
 }
 
 // Initialise, run all phases (switching to solo mode while the fringe is
@@ -904,7 +1250,7 @@ __device__ void solve_body(const SolveParams& p, const Grp& grp, unsigned char* 
   const uint64_t gtid = (uint64_t)grp.rank * nthr + tid;
   const bool leader = grp.rank == 0 && tid == 0;
   const Shared sh = carve(smem);
-  const Mode md = mode_of(p.crit, w.cur_in != nullptr);
+  const Mode md = mode_of(p);
   Stats st{0, 0, 0, 0};
 
   for (uint64_t v = gtid; v < n; v += gthreads) {
@@ -929,7 +1275,11 @@ __device__ void solve_body(const SolveParams& p, const Grp& grp, unsigned char* 
     ctl->heartbeat = 0;
     ctl->next_phase = 0;
     ctl->resume_relax = 0;
+    ctl->far_count = 0;
+    ctl->nf_tmp = 0;
   }
+  if (grp.rank == 0)
+    for (int b = tid; b < 2 * kNfBins; b += nthr) ctl->hist[b / kNfBins][b % kNfBins] = 0;
   if (!grp.sync()) return;
   if (leader) {
     w.vrec[p.source].d = 0;
@@ -946,10 +1296,38 @@ __device__ void solve_body(const SolveParams& p, const Grp& grp, unsigned char* 
   const bool dense_forced = (p.crit & SSSP_FRONTIER_DENSE) != 0;
   const uint32_t solo_cap = p.solo_max < kSoloCap ? p.solo_max : kSoloCap;
   unsigned int episodes = 0;
+  unsigned long long bound = kNoBound;  // near/far bound B (same in every block)
+  uint32_t nf_uses = 0;
   uint64_t k = 1;
   for (;;) {
     uint32_t nF = ldcg_u32(&ctl->slot[k % 4].qcount);
-    if (nF == 0) break;
+    uint32_t nf_code = 0;
+    if (k > (uint64_t)n + 1) {  // every phase settles a vertex: more phases mean a broken invariant
+      if (leader) atomicCAS(&ctl->err, 0, (int)SSSP_ERR_INTERNAL);
+      break;
+    }
+    if (md.nearfar) {
+      const uint32_t far = ldcg_u32(&ctl->far_count);
+      if (nF == 0 && far == 0) break;
+      const PhaseSlot* S0 = &ctl->slot[k % 4];
+      const unsigned long long T = md.use_out ? ldcg_u64(&S0->min_out) : ldcg_u64(&S0->min_d);
+      if (far > 0 && T > bound) {
+        if (!nf_refill(p, grp, md, k, sh, bound, nf_uses)) return;
+        nF = ldcg_u32(&ctl->slot[k % 4].qcount);
+        nf_code = kArmNfRefill;
+        if (nF == 0) {  // a refill always moves the vertex that attains T
+          if (leader) atomicCAS(&ctl->err, 0, (int)SSSP_ERR_INTERNAL);
+          break;
+        }
+      } else if (far == 0 && bound == kNoBound && nF >= p.nf_min) {
+        if (!nf_split(p, grp, md, k, sh, bound, nf_uses)) return;
+        nF = ldcg_u32(&ctl->slot[k % 4].qcount);
+        if (bound != kNoBound) nf_code = kArmNfRefill;
+      }
+      if (bound != kNoBound) nf_code |= kArmNfActive;
+    } else if (nF == 0) {
+      break;
+    }
     const bool fast_solo = md.fused && !dense_forced && nF <= solo_cap;
     const bool generic_solo = !md.fused && grp.size > 1 && nF <= p.solo_max;
     if (fast_solo || generic_solo) {
@@ -958,12 +1336,12 @@ __device__ void solve_body(const SolveParams& p, const Grp& grp, unsigned char* 
       bool resume_relax = false;
       if (grp.rank == 0) {
         if (fast_solo) {
-          k = solo_episode(p, md, k, smem, st, grp.size > 1, &resume_relax);
+          k = solo_episode(p, md, k, bound, nf_code, smem, st, grp.size > 1, &resume_relax);
         } else {
           // three-step kind: the generic phase on this block alone
           const Grp solo{grp.bar, grp.err, grp.limit, 0, 1};
-          while (nF != 0 && nF <= p.solo_max) {
-            run_phase(p, solo, md, k, sh, st);
+          while (nF != 0 && nF <= p.solo_max && k <= (uint64_t)n + 1) {
+            run_phase(p, solo, md, k, bound, 0u, sh, st);
             ++k;
             if (tid == 0) ctl->heartbeat = k;
             nF = ldcg_u32(&ctl->slot[k % 4].qcount);
@@ -994,12 +1372,12 @@ __device__ void solve_body(const SolveParams& p, const Grp& grp, unsigned char* 
       ++episodes;
       if (resume_relax) {
         const Arm arm = arm_for(p, ldcg_u32(&ctl->slot[k % 4].qcount));
-        if (!phase_relax(p, grp, md, arm, k, sh, st)) return;
+        if (!phase_relax(p, grp, md, arm, k, bound, true, sh, st)) return;
         ++k;
       }
       continue;
     }
-    if (!run_phase(p, grp, md, k, sh, st)) return;
+    if (!run_phase(p, grp, md, k, bound, nf_code, sh, st)) return;
     ++k;
   }
   if (leader) {
@@ -1037,9 +1415,14 @@ struct GroupSlot {
   unsigned int pad;
 };
 
+// Execution tuning of a batch launch (see sssp_tuning).
+struct BatchTuning {
+  uint32_t solo_max, solo_edges, nf_min, nf_target;
+};
+
 __global__ void __launch_bounds__(kThreads) k_solve_batch(const BatchItem* items, uint32_t count,
                                                            unsigned int* next, GroupSlot* groups, uint32_t bpg,
-                                                           uint32_t crit, uint32_t solo_max, uint32_t solo_edges,
+                                                           uint32_t crit, BatchTuning tu,
                                                            unsigned long long wait_ns, int* err,
                                                            unsigned long long* phases_out) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -1061,8 +1444,10 @@ __global__ void __launch_bounds__(kThreads) k_solve_batch(const BatchItem* items
     p.source = items[it].source;
     p.crit = crit;
     p.wait_ns = wait_ns;
-    p.solo_max = solo_max;
-    p.solo_edges = solo_edges;
+    p.solo_max = tu.solo_max;
+    p.solo_edges = tu.solo_edges;
+    p.nf_min = tu.nf_min;
+    p.nf_target = tu.nf_target;
     p.policy = nullptr;
     solve_body(p, grp, smem);
     if (*(volatile int*)err != 0) return;
@@ -1230,6 +1615,8 @@ sssp_status solve_one(sssp_graph* g, uint32_t source, uint32_t crit, uint64_t* d
   p.wait_ns = wait_limit_ns();
   p.solo_max = solo_max();
   p.solo_edges = solo_edges();
+  p.nf_min = nearfar_min();
+  p.nf_target = nearfar_target();
   p.policy = (crit & SSSP_POLICY_LEARNED) ? policy_weights() : nullptr;
 
   const int blocks = blocks_for(g->n);
@@ -1311,9 +1698,9 @@ sssp_status batch_enqueue(sssp_batch* b, cudaStream_t st) {
   SSSP_CUDA_TRY(cudaMemsetAsync(b->err, 0, sizeof(int), st));
   for (Workspace* w : b->ws) SSSP_CUDA_TRY(cudaMemsetAsync(w->ctl, 0, sizeof(Ctl), st));
   const int blocks = (int)(b->groups * b->bpg);
-  uint32_t solo = solo_max(), solo_e = solo_edges();
+  BatchTuning tu{solo_max(), solo_edges(), nearfar_min(), nearfar_target()};
   unsigned long long wait = wait_limit_ns();
-  void* args[] = {&b->items, &b->count, &b->next, &b->gslots, &b->bpg, &b->crit, &solo, &solo_e, &wait, &b->err, &b->phases};
+  void* args[] = {&b->items, &b->count, &b->next, &b->gslots, &b->bpg, &b->crit, &tu, &wait, &b->err, &b->phases};
   SSSP_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_solve_batch, dim3(blocks), dim3(kThreads), args,
                                             kSmemBytes, st));
   return SSSP_OK;

@@ -23,6 +23,8 @@ uint32_t solo_max();
 uint32_t batch_blocks_per_solve();
 uint32_t grid_blocks();
 uint32_t solo_edges();
+uint32_t nearfar_min();
+uint32_t nearfar_target();
 
 // Policy network weights loaded on the current device, or nullptr.
 const float* policy_weights();

@@ -174,6 +174,8 @@ extern "C" sssp_status sssp_solve_noalloc(uint32_t n, uint64_t m, const uint64_t
   p.wait_ns = wait_limit_ns();
   p.solo_max = solo_max();
   p.solo_edges = solo_edges();
+  p.nf_min = nearfar_min();
+  p.nf_target = nearfar_target();
   p.policy = nullptr;
   const uint64_t want = ((uint64_t)n + kTile - 1) / kTile;
   const int grid = (int)(want < (uint64_t)blocks ? (want > 0 ? want : 1) : blocks);

@@ -20,9 +20,21 @@ CRITS = [sp.IN_STATIC, sp.OUT_STATIC, sp.IN_OUT, sp.IN_SIMPLE, sp.OUT_SIMPLE, sp
 MODES = [0, sp.FRONTIER_DENSE, sp.FRONTIER_AUTO]
 
 
-# execution tunings that must not change any result: (solo_max, grid_blocks, solo_edges)
-TUNINGS = {"default": (4096, 0, 2048), "grid_only_3blk": (0, 3, 0), "solo_3blk": (8, 3, 4096),
-           "solo_edges_3blk": (4096, 3, 24), "one_block": (0, 1, 0), "one_block_solo": (4096, 1, 1 << 30)}
+# execution tunings that must not change any result (fields of sssp_tuning; the
+# near/far ones force the split on small fringes and a refill every few phases)
+TUNINGS = {
+    "default": {},
+    "grid_only_3blk": dict(solo_max_frontier=0, grid_blocks=3, solo_max_edges=0),
+    "solo_3blk": dict(solo_max_frontier=8, grid_blocks=3, solo_max_edges=4096),
+    "solo_edges_3blk": dict(solo_max_frontier=4096, grid_blocks=3, solo_max_edges=24),
+    "one_block": dict(solo_max_frontier=0, grid_blocks=1, solo_max_edges=0),
+    "one_block_solo": dict(solo_max_frontier=4096, grid_blocks=1, solo_max_edges=1 << 30),
+    "nearfar_grid_3blk": dict(solo_max_frontier=0, grid_blocks=3, nearfar_min_frontier=4, nearfar_target=6),
+    "nearfar_solo_3blk": dict(solo_max_frontier=4096, grid_blocks=3, solo_max_edges=64,
+                              nearfar_min_frontier=8, nearfar_target=40),
+    "nearfar_one_block": dict(solo_max_frontier=0, grid_blocks=1, nearfar_min_frontier=1, nearfar_target=1),
+    "nearfar_auto_target": dict(nearfar_min_frontier=256, nearfar_target=0),
+}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -38,8 +50,8 @@ def _device():
 
 @pytest.fixture(params=list(TUNINGS), ids=list(TUNINGS))
 def tuning(request):
-    solo, blocks, edges = TUNINGS[request.param]
-    sp.set_tuning(solo_max_frontier=solo, grid_blocks=blocks, solo_max_edges=edges)
+    sp.set_tuning()
+    sp.set_tuning(**TUNINGS[request.param])
     yield request.param
     sp.set_tuning()
 
@@ -299,3 +311,50 @@ def test_prepared_batch_replays():
             assert (sp.as_uint64(B.outs[k]) == oracle.dijkstra(g, s)).all()
             assert ph[k] == oracle.simulate(g, s, sp.IN_OUT).phases
     B.close()
+
+
+@pytest.mark.parametrize("crit", [sp.IN_OUT, sp.IN_STATIC, sp.OUT_STATIC], ids=["in_out", "in", "out"])
+def test_nearfar_split_runs_and_changes_nothing(crit):
+    """With a small split threshold the fringe is split and refilled many times
+    (trace arm bits 2 and 3); every per-phase figure still equals the oracle's."""
+    g = gg.workload(1).graphs[0]
+    G = sp.Graph.from_csr(g, reverse=True)
+    ref = oracle.dijkstra(g, 0)
+    sim = oracle.simulate(g, 0, crit, dist_ref=ref, trace=True)
+    try:
+        for tune in ["nearfar_grid_3blk", "nearfar_solo_3blk", "nearfar_auto_target"]:
+            sp.set_tuning()
+            sp.set_tuning(**TUNINGS[tune])
+            check(g, G, 0, crit, ref)
+            _, st, _, tr = sp.solve_trace(G, 0, crit, trace_cap=1 << 20)
+            arm = tr["arm"].astype(np.uint32)
+            assert (arm & 4).any() and (arm & 8).sum() >= 2, tune
+            q, f = tr["queued"], tr["frontier"]
+            assert (q <= f).all() and (q[(arm & 4) == 0] == f[(arm & 4) == 0]).all()
+            assert (q < f).any()  # some phases scanned only the near part
+            assert (tr["frontier"] == sim.trace[:, 0]).all()
+            assert (tr["settled"] == sim.trace[:, 1]).all()
+            assert (tr["min_d"] == sim.trace[:, 2]).all()  # thresholds exact after every refill
+            if crit & sp.OUT_STATIC:
+                assert (tr["min_out"] == sim.trace[:, 3]).all()
+        sp.set_tuning()
+        sp.set_tuning(**TUNINGS["nearfar_grid_3blk"])
+        _, _, _, tr = sp.solve_trace(G, 0, sp.SIMPLE, trace_cap=1 << 20)
+        assert not (tr["arm"].astype(np.uint32) & 12).any()  # dynamic IN: never split
+    finally:
+        sp.set_tuning()
+
+
+def test_trace_timestamps_are_ordered(tuning):
+    """Every phase record's interval lies after the previous one's (solo
+    episodes, hand-offs to the group, near/far refills included)."""
+    g = gg.workload(1).graphs[0]
+    G = sp.Graph.from_csr(g, reverse=True)
+    for crit in [sp.IN_OUT, sp.SIMPLE]:
+        _, st, _, tr = sp.solve_trace(G, 0, crit, trace_cap=1 << 20)
+        t0 = tr["t_start_ns"].astype(np.int64)
+        t1 = tr["t_end_ns"].astype(np.int64)
+        assert len(tr) == st["phases"] and (t0 > 0).all()
+        assert (t1 >= t0).all()
+        assert (t0[1:] >= t1[:-1]).all()
+        assert (tr["select_ns"].astype(np.int64) <= t1 - t0).all()
