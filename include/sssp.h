@@ -284,9 +284,12 @@ sssp_status sssp_solve_noalloc(uint32_t n, uint64_t m, const uint64_t* row_offse
  * scans, and a far part of vertices that no phase can settle before a bound B
  * on d(v) - inmin(v) is raised (0 = never split);
  * nearfar_target: vertices the near part is sized to when B is set or raised
- * (0 = chosen from n and the settled count of the last phase).  Applies to
- * launches made after the call; sssp_set_tuning(NULL) restores the defaults
- * (4096, 0, 0, 2048, 65536, 0). */
+ * (0 = chosen from n and the settled count of the last phase);
+ * nearfar_min_share: the split also needs a fringe of at least this many
+ * 256ths of n (a refill scans all n vertex records, which pays off only for a
+ * fringe that is a sizeable share of the graph; 0 = no such condition).
+ * Applies to launches made after the call; sssp_set_tuning(NULL) restores the
+ * defaults (4096, 0, 0, 2048, 65536, 0, 32). */
 typedef struct {
   uint32_t solo_max_frontier;
   uint32_t batch_blocks_per_solve;
@@ -294,7 +297,8 @@ typedef struct {
   uint32_t solo_max_edges;
   uint32_t nearfar_min_frontier;
   uint32_t nearfar_target;
-  uint32_t reserved[2];
+  uint32_t nearfar_min_share;
+  uint32_t reserved;
 } sssp_tuning;
 sssp_status sssp_set_tuning(const sssp_tuning* t);
 sssp_status sssp_get_tuning(sssp_tuning* t);

@@ -145,13 +145,13 @@ class Tuning(ctypes.Structure):
     _fields_ = [("solo_max_frontier", ctypes.c_uint32), ("batch_blocks_per_solve", ctypes.c_uint32),
                 ("grid_blocks", ctypes.c_uint32), ("solo_max_edges", ctypes.c_uint32),
                 ("nearfar_min_frontier", ctypes.c_uint32), ("nearfar_target", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32 * 2)]
+                ("nearfar_min_share", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 def set_tuning(**fields):
     """sssp_set_tuning; fields not given keep their current value (names as in
     sssp_tuning: solo_max_frontier, batch_blocks_per_solve, grid_blocks,
-    solo_max_edges, nearfar_min_frontier, nearfar_target).  set_tuning() with
+    solo_max_edges, nearfar_min_frontier, nearfar_target, nearfar_min_share).  set_tuning() with
     no argument restores the defaults."""
     if not fields:
         _check(lib().sssp_set_tuning(None))

@@ -16,6 +16,7 @@ std::atomic<uint32_t> g_grid_blocks{0};
 std::atomic<uint32_t> g_solo_edges{kSoloEdgesDefault};
 std::atomic<uint32_t> g_nf_min{kNearFarMinDefault};
 std::atomic<uint32_t> g_nf_target{0};
+std::atomic<uint32_t> g_nf_share{kNearFarShareDefault};
 }  // namespace
 
 uint32_t solo_max() { return g_solo_max.load(); }
@@ -24,6 +25,7 @@ uint32_t grid_blocks() { return g_grid_blocks.load(); }
 uint32_t solo_edges() { return g_solo_edges.load(); }
 uint32_t nearfar_min() { return g_nf_min.load(); }
 uint32_t nearfar_target() { return g_nf_target.load(); }
+uint32_t nearfar_share() { return g_nf_share.load(); }
 
 sssp_status fail(sssp_status st, const char* fmt, ...) {
   va_list ap;
@@ -94,6 +96,7 @@ extern "C" sssp_status sssp_set_tuning(const sssp_tuning* t) {
     sssp::g_solo_edges.store(sssp::kSoloEdgesDefault);
     sssp::g_nf_min.store(sssp::kNearFarMinDefault);
     sssp::g_nf_target.store(0);
+    sssp::g_nf_share.store(sssp::kNearFarShareDefault);
     return SSSP_OK;
   }
   sssp::g_solo_max.store(t->solo_max_frontier);
@@ -102,6 +105,7 @@ extern "C" sssp_status sssp_set_tuning(const sssp_tuning* t) {
   sssp::g_solo_edges.store(t->solo_max_edges);
   sssp::g_nf_min.store(t->nearfar_min_frontier);
   sssp::g_nf_target.store(t->nearfar_target);
+  sssp::g_nf_share.store(t->nearfar_min_share);
   return SSSP_OK;
 }
 
@@ -114,6 +118,7 @@ extern "C" sssp_status sssp_get_tuning(sssp_tuning* t) {
   t->solo_max_edges = sssp::g_solo_edges.load();
   t->nearfar_min_frontier = sssp::g_nf_min.load();
   t->nearfar_target = sssp::g_nf_target.load();
+  t->nearfar_min_share = sssp::g_nf_share.load();
   return SSSP_OK;
 }
 

@@ -156,8 +156,9 @@ struct Mode {
   bool nearfar;      // the fringe may be split into a near queue and a far part
 };
 
-// The near/far split needs static keys d(v) - inmin(v) (no IN-SIMPLE phase, so
-// no policy either) and fused thresholds, and n <= 2^30 for the far bit.
+// The near/far split needs static keys d(v) - inmin(v) (no IN-SIMPLE phase
+// while it is active: a policy is then limited to its IN-STATIC arms), fused
+// thresholds, and n <= 2^30 for the far bit.
 __device__ __forceinline__ Mode mode_of(const SolveParams& p) {
   const uint32_t crit = p.crit;
   Mode m;
@@ -167,7 +168,7 @@ __device__ __forceinline__ Mode mode_of(const SolveParams& p) {
   m.fused = !m.out_dyn && !m.dijk;
   const bool policy = (crit & SSSP_POLICY_LEARNED) != 0;
   m.use_in = (crit & (SSSP_IN_STATIC | SSSP_IN_SIMPLE)) != 0 || policy;
-  m.nearfar = m.fused && !policy && !(crit & SSSP_IN_SIMPLE) && p.nf_min != 0 && p.g.n <= kNearFarMaxVertices;
+  m.nearfar = m.fused && !(crit & SSSP_IN_SIMPLE) && p.nf_min != 0 && p.g.n <= kNearFarMaxVertices;
   return m;
 }
 
@@ -189,15 +190,26 @@ __device__ __forceinline__ Arm arm_for(const SolveParams& p, uint32_t nF) {
 // policy network on the phase-start features, evaluated by warp 0 of the block
 // and shared through shared memory.  Every thread of the block calls it; every
 // block computes the same arm from the same inputs.
-__device__ Arm choose_arm(const SolveParams& p, uint64_t k, uint32_t nF, uint64_t e_prev, uint64_t s_prev,
-                          uint64_t f_prev) {
-  if (!(p.crit & SSSP_POLICY_LEARNED) || p.policy == nullptr) return arm_for(p, nF);
+static_assert(kPolWeights * sizeof(float) == kSmemBytes - kPolicySmemOffset, "policy smem size");
+
+// The policy weights staged in dynamic shared memory by solve_body.
+__device__ __forceinline__ const float* policy_smem() {
+  extern __shared__ __align__(16) unsigned char smem_all[];
+  return reinterpret_cast<const float*>(smem_all + kPolicySmemOffset);
+}
+
+// allow_simple = false restricts the choice to the IN-STATIC arms (while the
+// fringe is split into near and far parts).
+// nQ: queue length (the dense/sparse choice without a policy); nF: |F|.
+__device__ Arm choose_arm(const SolveParams& p, uint64_t k, uint32_t nQ, uint32_t nF, uint64_t e_prev,
+                          uint64_t s_prev, uint64_t f_prev, bool allow_simple) {
+  if (!(p.crit & SSSP_POLICY_LEARNED) || p.policy == nullptr) return arm_for(p, nQ);
   __shared__ int s_arm;
   if ((threadIdx.x >> 5) == 0) {
     float f[kPolFeat], y[kPolArms];
     policy_features(f, nF, p.g.n, p.g.m, k, e_prev, s_prev, f_prev);
-    policy_forward_warp(p.policy, f, y);
-    if (threadIdx.x == 0) s_arm = policy_pick(y, p.ws.cur_in != nullptr);
+    policy_forward_warp(policy_smem(), f, y);
+    if (threadIdx.x == 0) s_arm = policy_pick(y, allow_simple && p.ws.cur_in != nullptr);
   }
   __syncthreads();
   Arm a;
@@ -238,7 +250,9 @@ __device__ __forceinline__ void reset_slot(PhaseSlot* s) {
 // its key du + c - inmin(t) exceeds the bound.  A new vertex that is far is
 // only counted (dfar); a far vertex whose stored word loses the bit is moved
 // to the near queue by the one relaxation whose atomicMin saw the bit go.
-// `fresh` asks the caller to append t to the next queue.
+// `fresh` asks the caller to append t to the next queue.  kNF = false is the
+// same code for a solve with no far vertex (B = kNoBound).
+template <bool kNF>
 __device__ __forceinline__ void relax_edge(const SolveParams& p, const Mode& md, uint32_t t, uint32_t cost,
                                            unsigned long long du, unsigned long long bound,
                                            unsigned long long& pd, unsigned long long& po, bool& fresh, int& dfar) {
@@ -247,20 +261,20 @@ __device__ __forceinline__ void relax_edge(const SolveParams& p, const Mode& md,
   if (rt.d & kSettledBit) return;
   const unsigned long long cand = du + cost;
   unsigned long long enc = cand;
-  if (md.nearfar && cand > bound + rt.im) enc |= kFarBit;
+  if (kNF && cand > bound + rt.im) enc |= kFarBit;
   if (enc < rt.d) {
     unsigned long long old = rt.d;
     if (rt.d == kUnexplored) {
       old = atomicMin(&w.vrec[t].d, enc);
       if (old == kUnexplored) {
         w.status[t] = kF;
-        if (enc & kFarBit) ++dfar;
+        if (kNF && (enc & kFarBit)) ++dfar;
         else fresh = true;
-      } else if (md.nearfar && (old & kFarBit) && !(enc & kFarBit)) {
+      } else if (kNF && (old & kFarBit) && !(enc & kFarBit)) {
         fresh = true;  // old < kUnexplored: t was far and is near now
         --dfar;
       }
-    } else if (md.nearfar && (rt.d & kFarBit) && !(enc & kFarBit)) {
+    } else if (kNF && (rt.d & kFarBit) && !(enc & kFarBit)) {
       old = atomicMin(&w.vrec[t].d, enc);
       if (old & kFarBit) {  // old <= rt.d < kUnexplored
         fresh = true;
@@ -277,6 +291,13 @@ __device__ __forceinline__ void relax_edge(const SolveParams& p, const Mode& md,
       }
     }
   }
+}
+
+// Relax-list entry `slot` covers edges [base, base + deg) of the phase's edge
+// sequence: it owns the first edge of every tile that starts in that range.
+__device__ __forceinline__ void mark_tile_owner(uint32_t* owner, uint32_t slot, uint32_t base, uint32_t deg) {
+  const uint64_t end = (uint64_t)base + deg;
+  for (uint64_t t = ((uint64_t)base + kTile - 1) / kTile; t * kTile < end; ++t) owner[t] = slot;
 }
 
 // ---------------------------------------------------------------------------
@@ -466,11 +487,13 @@ __device__ bool phase_select(const SolveParams& p, const Grp& grp, const Mode& m
         ++kslot;
       }
       if (((selm >> j) & 1u) && rd[j].y > 0) {
-        if (rslot < n)
+        if (rslot < n) {
           *reinterpret_cast<ulonglong2*>(&w.sp[rslot]) =
               make_ulonglong2(rr[j].d, (unsigned long long)rd[j].x | ((unsigned long long)ebase << 32));
-        else
+          if (w.tile_owner) mark_tile_owner(w.tile_owner, rslot, ebase, rd[j].y);
+        } else {
           atomicCAS(&ctl->err, 0, (int)SSSP_ERR_INTERNAL);
+        }
         ++rslot;
         ebase += rd[j].y;
       }
@@ -485,6 +508,7 @@ __device__ bool phase_select(const SolveParams& p, const Grp& grp, const Mode& m
 // Step C of phase k (relax every out-edge of S', edge-balanced tiles), then
 // the end-of-phase barrier, counters and trace.  Every block of the group
 // calls it.  Returns false if a barrier gave up.
+template <bool kNF>
 __device__ bool phase_relax(const SolveParams& p, const Grp& grp, const Mode& md, const Arm arm, uint64_t k,
                             unsigned long long bound, bool resumed, const Shared& sh, Stats& st) {
   const GraphView& g = p.g;
@@ -509,14 +533,20 @@ __device__ bool phase_relax(const SolveParams& p, const Grp& grp, const Mode& md
     const uint32_t e1 = (uint64_t)e0 + kTile < E ? e0 + kTile : E;
     if (warp == 0) {
       uint32_t lo = 0, hi = nS - 1;
-      if (!(e0 == 0 && e1 == E)) {
+      if (w.tile_owner) {
+        // entries lo .. hi intersect the tile (hi may start just past it, and is
+        // then dropped by the kTile cap below: the per-edge search never picks it)
+        lo = ldcg_u32(&w.tile_owner[tile]);
+        if (e1 < E) hi = ldcg_u32(&w.tile_owner[tile + 1]);
+      } else if (!(e0 == 0 && e1 == E)) {
         lo = warp_upper_bound_sp(w.sp, nS, e0) - 1;
         hi = warp_upper_bound_sp(w.sp, nS, e1 - 1) - 1;
       }
       if (lane == 0) { sh.s_range[0] = lo; sh.s_range[1] = hi; }
     }
     __syncthreads();
-    const uint32_t lo = sh.s_range[0], cnt = sh.s_range[1] - sh.s_range[0] + 1;
+    const uint32_t lo = sh.s_range[0];
+    const uint32_t cnt = min(sh.s_range[1] - sh.s_range[0] + 1, (uint32_t)kTile);
     for (uint32_t j = tid; j < cnt; j += nthr) {
       const SpEnt e = ldcg_sp(&w.sp[lo + j]);
       sh.s_base[j] = e.base;
@@ -538,7 +568,7 @@ __device__ bool phase_relax(const SolveParams& p, const Grp& grp, const Mode& md
         }
         const uint2 ed = __ldg(&g.edges[sh.s_row[a] + (e - sh.s_base[a])]);
         bool fresh = false;
-        relax_edge(p, md, ed.x, ed.y, sh.s_d[a], bound, pd, po, fresh, dfar);
+        relax_edge<kNF>(p, md, ed.x, ed.y, sh.s_d[a], bound, pd, po, fresh, dfar);
         if (fresh) {
           fv[it] = ed.x;
           fmask |= 1u << it;
@@ -561,7 +591,7 @@ __device__ bool phase_relax(const SolveParams& p, const Grp& grp, const Mode& md
     __syncthreads();
   }
   if (md.fused) block_min2_to_global(pd, po, &S1->min_d, md.use_out ? &S1->min_out : nullptr, sh.red);
-  if (md.nearfar) {  // far-part count: one atomic per block (the barrier above orders scratch reuse)
+  if (kNF) {  // far-part count: one atomic per block (the barrier above orders scratch reuse)
     uint32_t tf;
     block_exclusive_scan((uint32_t)dfar, sh.scan, &tf);
     if (tid == 0 && tf) atomicAdd(&ctl->far_count, tf);
@@ -599,12 +629,61 @@ __device__ bool phase_relax(const SolveParams& p, const Grp& grp, const Mode& md
 __device__ __forceinline__ bool run_phase(const SolveParams& p, const Grp& grp, const Mode& md, uint64_t k,
                                           unsigned long long bound, uint32_t nf_code, const Shared& sh, Stats& st) {
   const PhaseSlot* prev = &p.ws.ctl->slot[(k + 3) % 4];
-  const Arm arm = choose_arm(p, k, ldcg_u32(&p.ws.ctl->slot[k % 4].qcount),
-                             (uint32_t)ldcg_u64(&prev->relax_packed), ldcg_u32(&prev->settled_now),
-                             ldcg_u32(&prev->qcount));
+  const uint32_t nQ = ldcg_u32(&p.ws.ctl->slot[k % 4].qcount);
+  const uint32_t nF = nQ + (md.nearfar ? ldcg_u32(&p.ws.ctl->far_count) : 0u);
+  const Arm arm = choose_arm(p, k, nQ, nF, (uint32_t)ldcg_u64(&prev->relax_packed), ldcg_u32(&prev->settled_now),
+                             ldcg_u32(&prev->fsize), bound == kNoBound);
   if (grp.rank == 0 && threadIdx.x == 0) p.ws.ctl->slot[k % 4].arm = arm_code(arm, grp.size == 1) | nf_code;
   if (!phase_select(p, grp, md, arm, k, sh, st)) return false;
-  return phase_relax(p, grp, md, arm, k, bound, false, sh, st);
+  return bound != kNoBound ? phase_relax<true>(p, grp, md, arm, k, bound, false, sh, st)
+                           : phase_relax<false>(p, grp, md, arm, k, bound, false, sh, st);
+}
+
+// Relax step of a solo phase: the warps of the block stride over the relax
+// list's edges; vertices new to the next queue get slots from a shared counter
+// (slots past kSoloCap go to the global queue at the same index).
+struct SoloRelax {
+  const unsigned long long* sp_d;
+  const uint32_t* sp_row;
+  const uint32_t* sp_base;
+  uint32_t nS, E;
+  uint32_t* sqn;
+  uint32_t* gqn;
+  unsigned int* qn;
+};
+
+template <bool kNF>
+__device__ __forceinline__ void solo_relax(const SolveParams& p, const Mode& md, const SoloRelax& r,
+                                           unsigned long long bound, unsigned long long& pd, unsigned long long& po,
+                                           int& dfar) {
+  const unsigned int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (uint32_t eb = warp * 32; eb < r.E; eb += blockDim.x) {
+    const uint32_t e = eb + lane;
+    bool fresh = false;
+    uint32_t t = 0;
+    if (e < r.E) {
+      uint32_t a = 0, b = r.nS;
+      while (b - a > 1) {
+        const uint32_t mid = (a + b) >> 1;
+        if (r.sp_base[mid] <= e) a = mid; else b = mid;
+      }
+      const uint2 ed = __ldg(&p.g.edges[r.sp_row[a] + (e - r.sp_base[a])]);
+      t = ed.x;
+      relax_edge<kNF>(p, md, t, ed.y, r.sp_d[a], bound, pd, po, fresh, dfar);
+    }
+    const unsigned int fmask = __ballot_sync(0xFFFFFFFFu, fresh);
+    if (fmask) {
+      unsigned int b0 = 0;
+      if (lane == 0) b0 = atomicAdd(r.qn, (unsigned int)__popc(fmask));
+      b0 = __shfl_sync(0xFFFFFFFFu, b0, 0);
+      if (fresh) {
+        const uint32_t slot = b0 + __popc(fmask & ((1u << lane) - 1u));
+        if (slot < kSoloCap) r.sqn[slot] = t;
+        else if (slot < p.g.n) r.gqn[slot] = t;
+        else atomicCAS(&p.ws.ctl->err, 0, (int)SSSP_ERR_INTERNAL);
+      }
+    }
+  }
 }
 
 // Solo episode (fused thresholds only): this block runs phases k, k+1, ...
@@ -620,7 +699,8 @@ __device__ __forceinline__ bool run_phase(const SolveParams& p, const Grp& grp, 
 // handoff), or the state after a grid selection step of phase k (handoff).
 // All threads of the block call it.
 __device__ uint64_t solo_episode(const SolveParams& p, const Mode& md, uint64_t k, unsigned long long bound,
-                                 uint32_t nf_code, unsigned char* smem, Stats& st, bool can_handoff, bool* handoff) {
+                                 uint32_t nf_code, unsigned char* smem, Stats& st_shared, bool can_handoff,
+                                 bool* handoff) {
   const GraphView& g = p.g;
   const SolveWS& w = p.ws;
   Ctl* ctl = w.ctl;
@@ -647,9 +727,11 @@ __device__ uint64_t solo_episode(const SolveParams& p, const Mode& md, uint64_t 
   // counters of the previous phase (policy features)
   uint64_t e_prev = (uint32_t)ldcg_u64(&ctl->slot[(k + 3) % 4].relax_packed);
   uint64_t s_prev = ldcg_u32(&ctl->slot[(k + 3) % 4].settled_now);
-  uint64_t f_prev = ldcg_u32(&ctl->slot[(k + 3) % 4].qcount);
+  uint64_t f_prev = ldcg_u32(&ctl->slot[(k + 3) % 4].fsize);
   uint32_t nF = ldcg_u32(&ctl->slot[k % 4].qcount);
-  uint32_t far = md.nearfar ? ldcg_u32(&ctl->far_count) : 0u;  // far part of F (not in the queues)
+  const bool kNF = bound != kNoBound;
+  uint32_t far = kNF ? ldcg_u32(&ctl->far_count) : 0u;  // far part of F (not in the queues)
+  Stats st = st_shared;  // thread 0's running counters, in registers for the episode
   Arm arm{false, false, -1};
   unsigned int since_pick = 0;
   unsigned long long minD = ldcg_u64(&ctl->slot[k % 4].min_d);
@@ -666,13 +748,13 @@ __device__ uint64_t solo_episode(const SolveParams& p, const Mode& md, uint64_t 
     uint32_t* gqn = w.q[cur ^ 1];
     // the policy is evaluated on the first phase of the episode and every 4th
     // phase after it (the choice is logged per phase either way)
-    if (since_pick == 0) arm = choose_arm(p, k, nF, e_prev, s_prev, f_prev);
+    if (since_pick == 0) arm = choose_arm(p, k, nF, nF + far, e_prev, s_prev, f_prev, !kNF);
     since_pick = (since_pick + 1) & 3u;
     const bool in_dyn = md.use_in && arm.in_simple && w.cur_in != nullptr;
     const uint32_t fs = nF + far;  // |F| at the start of the phase
     unsigned long long t0 = 0, t_sel = 0;
     if (tid == 0) {
-      t0 = globaltimer_ns();
+      if (w.trace) t0 = globaltimer_ns();
       s_qn = 0;
       s_settled = 0;
       s_relax = 0;
@@ -685,7 +767,10 @@ __device__ uint64_t solo_episode(const SolveParams& p, const Mode& md, uint64_t 
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const uint32_t i = i0 + j * nthr;
-        if (i < nF) r[j] = ldcg_vrec(&w.vrec[sq[i]]);
+        if (i < nF) {
+          const uint32_t v = sq[i];
+          r[j] = ldcg_vrec(&w.vrec[v]);
+        }
       }
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
@@ -814,9 +899,11 @@ __device__ uint64_t solo_episode(const SolveParams& p, const Mode& md, uint64_t 
     const uint32_t nS = (uint32_t)(packed >> 32), E = (uint32_t)packed;
     if (can_handoff && E > p.solo_edges) {
       // state of a grid selection step of phase k, in global memory
-      for (uint32_t j = tid; j < nS; j += nthr)
+      for (uint32_t j = tid; j < nS; j += nthr) {
         *reinterpret_cast<ulonglong2*>(&w.sp[j]) =
             make_ulonglong2(sp_d[j], (unsigned long long)sp_row[j] | ((unsigned long long)sp_base[j] << 32));
+        if (w.tile_owner) mark_tile_owner(w.tile_owner, j, sp_base[j], (j + 1 < nS ? sp_base[j + 1] : E) - sp_base[j]);
+      }
       const uint32_t kept = s_qn;
       const uint32_t nk = kept < kSoloCap ? kept : kSoloCap;
       for (uint32_t j = tid; j < nk; j += nthr) gqn[j] = sqn[j];
@@ -840,6 +927,7 @@ __device__ uint64_t solo_episode(const SolveParams& p, const Mode& md, uint64_t 
         S1->qcount = kept;
         S1->min_d = s_thr_d;
         S1->min_out = s_thr_o;
+        st_shared = st;
       }
       __threadfence();
       __syncthreads();
@@ -847,40 +935,16 @@ __device__ uint64_t solo_episode(const SolveParams& p, const Mode& md, uint64_t 
       return k;
     }
     // ---- C: relax
-    if (tid == 0) t_sel = globaltimer_ns();
+    if (tid == 0 && w.trace) t_sel = globaltimer_ns();
     pd = kInf64;
     po = kInf64;
     int dfar = 0;
-    for (uint32_t eb = warp * 32; eb < E; eb += nthr) {
-      const uint32_t e = eb + lane;
-      bool fresh = false;
-      uint32_t t = 0;
-      if (e < E) {
-        uint32_t a = 0, b = nS;
-        while (b - a > 1) {
-          const uint32_t mid = (a + b) >> 1;
-          if (sp_base[mid] <= e) a = mid; else b = mid;
-        }
-        const uint2 ed = __ldg(&g.edges[sp_row[a] + (e - sp_base[a])]);
-        t = ed.x;
-        relax_edge(p, md, t, ed.y, sp_d[a], bound, pd, po, fresh, dfar);
-      }
-      const unsigned int fmask = __ballot_sync(0xFFFFFFFFu, fresh);
-      if (fmask) {
-        unsigned int b0 = 0;
-        if (lane == 0) b0 = atomicAdd(&s_qn, (unsigned int)__popc(fmask));
-        b0 = __shfl_sync(0xFFFFFFFFu, b0, 0);
-        if (fresh) {
-          const uint32_t slot = b0 + __popc(fmask & ((1u << lane) - 1u));
-          if (slot < kSoloCap) sqn[slot] = t;
-          else if (slot < n) gqn[slot] = t;
-          else atomicCAS(&ctl->err, 0, (int)SSSP_ERR_INTERNAL);
-        }
-      }
-    }
+    const SoloRelax sr{sp_d, sp_row, sp_base, nS, E, sqn, gqn, &s_qn};
+    if (kNF) solo_relax<true>(p, md, sr, bound, pd, po, dfar);
+    else solo_relax<false>(p, md, sr, bound, pd, po, dfar);
     pd = warp_min_u64(pd);
     po = warp_min_u64(po);
-    if (md.nearfar) dfar = __reduce_add_sync(0xFFFFFFFFu, dfar);
+    if (kNF) dfar = __reduce_add_sync(0xFFFFFFFFu, dfar);
     if (lane == 0) {
       if (pd != kInf64) atomicMin(&s_thr_d, pd);
       if (po != kInf64 && md.use_out) atomicMin(&s_thr_o, po);
@@ -917,14 +981,14 @@ __device__ uint64_t solo_episode(const SolveParams& p, const Mode& md, uint64_t 
     minOut = s_thr_o;
     e_prev = E;
     s_prev = s_settled;
-    f_prev = nF;
+    f_prev = fs;
     nF = nFn;
-    far += (uint32_t)s_dfar;
+    if (kNF) far += (uint32_t)s_dfar;
     ++k;
     __syncthreads();  // shared counters are read before the next phase resets them
     if (nF == 0 || nF > cap || k > (uint64_t)n + 1) break;
     // thresholds above the bound are exact only after the far part is scanned
-    if (far > 0 && (md.use_out ? minOut : minD) > bound) break;
+    if (kNF && far > 0 && (md.use_out ? minOut : minD) > bound) break;
   }
   // hand the state back in global memory for phase k
   {
@@ -934,6 +998,7 @@ __device__ uint64_t solo_episode(const SolveParams& p, const Mode& md, uint64_t 
     for (uint32_t i = tid; i < ns; i += nthr) gq[i] = sq[i];
   }
   if (tid == 0) {
+    st_shared = st;
     PhaseSlot* S0 = &ctl->slot[k % 4];
     reset_slot(S0);
     reset_slot(&ctl->slot[(k + 1) % 4]);
@@ -944,7 +1009,7 @@ __device__ uint64_t solo_episode(const SolveParams& p, const Mode& md, uint64_t 
     PhaseSlot* Sp = &ctl->slot[(k + 3) % 4];  // the last solo phase, for the policy's features
     Sp->relax_packed = e_prev;
     Sp->settled_now = (uint32_t)s_prev;
-    Sp->qcount = (uint32_t)f_prev;
+    Sp->fsize = (uint32_t)f_prev;
   }
   __threadfence();
   __syncthreads();
@@ -1134,6 +1199,10 @@ __device__ __noinline__ bool nf_refill(const SolveParams& p, const Grp& grp, con
   uint32_t* hist = sh.s_base;
   ulonglong2* tmp = reinterpret_cast<ulonglong2*>(w.sp);
   __shared__ unsigned int s_fcnt;
+  // |F| now: read before the first barrier, since R2 of faster blocks changes
+  // both counts while slower ones still pick the bin (every block must pick
+  // the same B)
+  const uint32_t fringe = ldcg_u32(&S0->qcount) + ldcg_u32(&ctl->far_count);
   // this block's vertex range [lo, hi)
   const uint64_t per = ((uint64_t)n + grp.size - 1) / grp.size;
   const uint64_t lo = (uint64_t)grp.rank * per;
@@ -1188,7 +1257,7 @@ __device__ __noinline__ bool nf_refill(const SolveParams& p, const Grp& grp, con
   const unsigned long long minD = a_d < f_d ? a_d : f_d;
   const unsigned long long minOut = a_o < f_o ? a_o : f_o;
   const unsigned long long T = md.use_out ? minOut : minD;
-  const int b = nf_pick_bin(gh, nf_target(p, k, ldcg_u32(&S0->qcount) + ldcg_u32(&ctl->far_count)), sh);
+  const int b = nf_pick_bin(gh, nf_target(p, k, fringe), sh);
   const unsigned long long e = b >= kNfBins ? kNoBound : nf_bin_upper(b);
   unsigned long long B = e >= kNoBound - bound ? kNoBound : bound + e;
   if (B < T) B = T >= kNoBound ? kNoBound : T;
@@ -1251,7 +1320,20 @@ __device__ void solve_body(const SolveParams& p, const Grp& grp, unsigned char* 
   const bool leader = grp.rank == 0 && tid == 0;
   const Shared sh = carve(smem);
   const Mode md = mode_of(p);
-  Stats st{0, 0, 0, 0};
+  // Counters and the near/far bound live in shared memory: they are touched
+  // once per phase at most, and keeping them out of registers leaves the
+  // phase loops more room.
+  __shared__ Stats s_st;
+  __shared__ unsigned long long s_bound;
+  Stats& st = s_st;
+  if (tid == 0) {
+    s_st = Stats{0, 0, 0, 0};
+    s_bound = kNoBound;
+  }
+  if ((p.crit & SSSP_POLICY_LEARNED) && p.policy) {  // (published by the first barrier below)
+    float* pw = reinterpret_cast<float*>(smem + kPolicySmemOffset);
+    for (int i = tid; i < kPolWeights; i += nthr) pw[i] = __ldg(&p.policy[i]);
+  }
 
   for (uint64_t v = gtid; v < n; v += gthreads) {
     const uint32_t im = __ldg(&g.in_min[v]), om = __ldg(&g.out_min[v]);
@@ -1296,7 +1378,7 @@ __device__ void solve_body(const SolveParams& p, const Grp& grp, unsigned char* 
   const bool dense_forced = (p.crit & SSSP_FRONTIER_DENSE) != 0;
   const uint32_t solo_cap = p.solo_max < kSoloCap ? p.solo_max : kSoloCap;
   unsigned int episodes = 0;
-  unsigned long long bound = kNoBound;  // near/far bound B (same in every block)
+  unsigned long long& bound = s_bound;  // near/far bound B (same in every block)
   uint32_t nf_uses = 0;
   uint64_t k = 1;
   for (;;) {
@@ -1319,10 +1401,21 @@ __device__ void solve_body(const SolveParams& p, const Grp& grp, unsigned char* 
           if (leader) atomicCAS(&ctl->err, 0, (int)SSSP_ERR_INTERNAL);
           break;
         }
-      } else if (far == 0 && bound == kNoBound && nF >= p.nf_min) {
-        if (!nf_split(p, grp, md, k, sh, bound, nf_uses)) return;
-        nF = ldcg_u32(&ctl->slot[k % 4].qcount);
-        if (bound != kNoBound) nf_code = kArmNfRefill;
+      } else if (far == 0 && bound == kNoBound && nF >= p.nf_min &&
+                 (uint64_t)nF * 256 >= (uint64_t)p.nf_share * n) {
+        // with a policy, the split is its choice too: only when it picks an
+        // IN-STATIC arm for this phase (the split then keeps it to those)
+        bool split = true;
+        if ((p.crit & SSSP_POLICY_LEARNED) && p.policy) {
+          const PhaseSlot* prev = &ctl->slot[(k + 3) % 4];
+          split = choose_arm(p, k, nF, nF, (uint32_t)ldcg_u64(&prev->relax_packed), ldcg_u32(&prev->settled_now),
+                             ldcg_u32(&prev->fsize), true).index < 2;
+        }
+        if (split) {
+          if (!nf_split(p, grp, md, k, sh, bound, nf_uses)) return;
+          nF = ldcg_u32(&ctl->slot[k % 4].qcount);
+          if (bound != kNoBound) nf_code = kArmNfRefill;
+        }
       }
       if (bound != kNoBound) nf_code |= kArmNfActive;
     } else if (nF == 0) {
@@ -1372,7 +1465,9 @@ __device__ void solve_body(const SolveParams& p, const Grp& grp, unsigned char* 
       ++episodes;
       if (resume_relax) {
         const Arm arm = arm_for(p, ldcg_u32(&ctl->slot[k % 4].qcount));
-        if (!phase_relax(p, grp, md, arm, k, bound, true, sh, st)) return;
+        const bool ok = bound != kNoBound ? phase_relax<true>(p, grp, md, arm, k, bound, true, sh, st)
+                                          : phase_relax<false>(p, grp, md, arm, k, bound, true, sh, st);
+        if (!ok) return;
         ++k;
       }
       continue;
@@ -1417,7 +1512,7 @@ struct GroupSlot {
 
 // Execution tuning of a batch launch (see sssp_tuning).
 struct BatchTuning {
-  uint32_t solo_max, solo_edges, nf_min, nf_target;
+  uint32_t solo_max, solo_edges, nf_min, nf_target, nf_share;
 };
 
 __global__ void __launch_bounds__(kThreads) k_solve_batch(const BatchItem* items, uint32_t count,
@@ -1448,6 +1543,7 @@ __global__ void __launch_bounds__(kThreads) k_solve_batch(const BatchItem* items
     p.solo_edges = tu.solo_edges;
     p.nf_min = tu.nf_min;
     p.nf_target = tu.nf_target;
+    p.nf_share = tu.nf_share;
     p.policy = nullptr;
     solve_body(p, grp, smem);
     if (*(volatile int*)err != 0) return;
@@ -1521,19 +1617,21 @@ void workspace_free(Workspace* ws) {
   cudaFree(ws->cur_out);
   cudaFree(ws->cur_in);
   cudaFree(ws->im_dyn);
+  cudaFree(ws->tile_owner);
   cudaFree(ws->dist);
   cudaFree(ws->ctl);
   cudaFreeHost(ws->ctl_host);
   delete ws;
 }
 
-sssp_status workspace_alloc(uint32_t n, bool want_cursors, bool want_dist, Workspace** out) {
+sssp_status workspace_alloc(uint32_t n, uint64_t m, bool want_cursors, bool want_dist, Workspace** out) {
   Workspace* ws = new (std::nothrow) Workspace();
   if (!ws) return fail(SSSP_ERR_OUT_OF_MEMORY, "host allocation failed");
   ws->n = n;
   sssp_status s = SSSP_OK;
   if ((s = dev_alloc(&ws->vrec, n)) || (s = dev_alloc(&ws->status, n)) || (s = dev_alloc(&ws->q0, n)) ||
-      (s = dev_alloc(&ws->q1, n)) || (s = dev_alloc(&ws->sp, n)) || (s = dev_alloc(&ws->ctl, 1))) {
+      (s = dev_alloc(&ws->q1, n)) || (s = dev_alloc(&ws->sp, n)) || (s = dev_alloc(&ws->ctl, 1)) ||
+      (s = dev_alloc(&ws->tile_owner, m / kTile + 2))) {
     workspace_free(ws);
     return s;
   }
@@ -1556,7 +1654,7 @@ sssp_status workspace_alloc(uint32_t n, bool want_cursors, bool want_dist, Works
 
 sssp_status workspace_get(sssp_graph* g, Workspace** out) {
   if (!g->ws) {
-    sssp_status s = workspace_alloc(g->n, true, true, &g->ws);
+    sssp_status s = workspace_alloc(g->n, g->m, true, true, &g->ws);
     if (s != SSSP_OK) return s;
   }
   *out = g->ws;
@@ -1577,6 +1675,7 @@ SolveWS ws_view(Workspace* ws, unsigned long long* dist, uint32_t crit, bool has
   w.cur_out = (crit & SSSP_OUT_SIMPLE) ? ws->cur_out : nullptr;
   w.cur_in = ((crit & (SSSP_IN_SIMPLE | SSSP_POLICY_LEARNED)) && has_reverse) ? ws->cur_in : nullptr;
   w.im_dyn = w.cur_in ? ws->im_dyn : nullptr;
+  w.tile_owner = ws->tile_owner;
   w.ctl = ws->ctl;
   return w;
 }
@@ -1617,6 +1716,7 @@ sssp_status solve_one(sssp_graph* g, uint32_t source, uint32_t crit, uint64_t* d
   p.solo_edges = solo_edges();
   p.nf_min = nearfar_min();
   p.nf_target = nearfar_target();
+  p.nf_share = nearfar_share();
   p.policy = (crit & SSSP_POLICY_LEARNED) ? policy_weights() : nullptr;
 
   const int blocks = blocks_for(g->n);
@@ -1698,7 +1798,7 @@ sssp_status batch_enqueue(sssp_batch* b, cudaStream_t st) {
   SSSP_CUDA_TRY(cudaMemsetAsync(b->err, 0, sizeof(int), st));
   for (Workspace* w : b->ws) SSSP_CUDA_TRY(cudaMemsetAsync(w->ctl, 0, sizeof(Ctl), st));
   const int blocks = (int)(b->groups * b->bpg);
-  BatchTuning tu{solo_max(), solo_edges(), nearfar_min(), nearfar_target()};
+  BatchTuning tu{solo_max(), solo_edges(), nearfar_min(), nearfar_target(), nearfar_share()};
   unsigned long long wait = wait_limit_ns();
   void* args[] = {&b->items, &b->count, &b->next, &b->gslots, &b->bpg, &b->crit, &tu, &wait, &b->err, &b->phases};
   SSSP_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_solve_batch, dim3(blocks), dim3(kThreads), args,
@@ -1741,7 +1841,7 @@ sssp_status batch_build(sssp_graph* const* graphs, const uint32_t* sources, uint
   const bool cursors = (crit & (SSSP_IN_SIMPLE | SSSP_OUT_SIMPLE)) != 0;
   for (uint32_t k = 0; k < count; ++k) {
     const uint32_t i = order[k];
-    if ((s = workspace_alloc(graphs[i]->n, cursors, false, &b->ws[k])) != SSSP_OK) {
+    if ((s = workspace_alloc(graphs[i]->n, graphs[i]->m, cursors, false, &b->ws[k])) != SSSP_OK) {
       batch_free(b);
       return s;
     }

@@ -15,6 +15,7 @@ constexpr uint32_t kSoloCap = 4096;
 constexpr uint32_t kSoloMaxDefault = kSoloCap;     // fringe size limit
 constexpr uint32_t kSoloEdgesDefault = 2048;       // relax edges above which a solo phase hands off
 constexpr uint32_t kNearFarMinDefault = 65536;     // fringe size at which the near/far split starts
+constexpr uint32_t kNearFarShareDefault = 32;      // ... and fringe share of n, in 256ths
 constexpr size_t kGridSmem = 66 * sizeof(unsigned long long)                               // reduction scratch, bases
                              + kTile * (2 * sizeof(uint32_t) + sizeof(unsigned long long))  // relax tile
                              + 36 * sizeof(uint32_t);                                        // range, scan
@@ -26,7 +27,11 @@ constexpr size_t kSoloSmem = 64 * sizeof(unsigned long long)                    
 // Graphs whose edges and vertex records take at most this many bytes are
 // prefetched into L2 when a solve starts (L2 holds 126 MiB).
 constexpr uint64_t kL2PrefetchBytes = 96ull << 20;
-constexpr size_t kSmemBytes = kGridSmem > kSoloSmem ? kGridSmem : kSoloSmem;
+// The phase layouts share one region; the policy network's weights follow it
+// (staged once per solve, so an inference reads shared memory only).
+constexpr size_t kPhaseSmem = kGridSmem > kSoloSmem ? kGridSmem : kSoloSmem;
+constexpr size_t kPolicySmemOffset = (kPhaseSmem + 15) / 16 * 16;
+constexpr size_t kSmemBytes = kPolicySmemOffset + 1476 * sizeof(float);
 
 struct SolveParams {
   GraphView g;
@@ -38,6 +43,7 @@ struct SolveParams {
   uint32_t solo_edges;  // relax edges above which a solo phase hands off to the group
   uint32_t nf_min;      // fringe size at which the near/far split starts (0 = never)
   uint32_t nf_target;   // near-part size aimed at when the bound is set (0 = automatic)
+  uint32_t nf_share;    // the split also needs |F| >= nf_share * n / 256
   const float* policy;  // policy network weights (device) or nullptr
 };
 

@@ -25,6 +25,7 @@ uint32_t grid_blocks();
 uint32_t solo_edges();
 uint32_t nearfar_min();
 uint32_t nearfar_target();
+uint32_t nearfar_share();
 
 // Policy network weights loaded on the current device, or nullptr.
 const float* policy_weights();
@@ -81,6 +82,7 @@ struct Workspace {
   uint32_t* cur_out;
   uint32_t* cur_in;
   uint32_t* im_dyn;
+  uint32_t* tile_owner;      // [m / kTile + 2] relax-list entry holding the first edge of each tile
   unsigned long long* dist;  // used when the caller's distance buffer is host memory
   Ctl* ctl;
   Ctl* ctl_host;  // pinned mirror for read-back
@@ -88,7 +90,7 @@ struct Workspace {
 
 GraphView view_of(const sssp_graph* g);
 sssp_status workspace_get(sssp_graph* g, Workspace** out);
-sssp_status workspace_alloc(uint32_t n, bool want_cursors, bool want_dist, Workspace** out);
+sssp_status workspace_alloc(uint32_t n, uint64_t m, bool want_cursors, bool want_dist, Workspace** out);
 void workspace_free(Workspace* ws);
 
 }  // namespace sssp

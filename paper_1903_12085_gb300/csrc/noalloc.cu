@@ -176,6 +176,7 @@ extern "C" sssp_status sssp_solve_noalloc(uint32_t n, uint64_t m, const uint64_t
   p.solo_edges = solo_edges();
   p.nf_min = nearfar_min();
   p.nf_target = nearfar_target();
+  p.nf_share = nearfar_share();
   p.policy = nullptr;
   const uint64_t want = ((uint64_t)n + kTile - 1) / kTile;
   const int grid = (int)(want < (uint64_t)blocks ? (want > 0 ? want : 1) : blocks);

@@ -12,8 +12,9 @@
 // phase settles and what the phase costs.  The network maps 8 features of the
 // phase-start state to 4 outputs, the predicted log2 of the phase time per
 // settled vertex for each arm; the phase takes the arm with the smallest
-// prediction (IN-SIMPLE arms only when the in-edge CSR exists; a non-finite
-// prediction falls back to arm 0, the paper's IN+OUT).
+// prediction if it beats arm 0 by a margin, else arm 0, the paper's IN+OUT
+// (IN-SIMPLE arms only when the in-edge CSR exists and the fringe is not split
+// into near and far parts; a non-finite prediction falls back to arm 0).
 //
 // Features (float32, all cheap and identical in every block):
 //   f0 = log2(1 + |F|) / 24          f4 = log2(1 + k) / 16     (k = phase index)
@@ -55,28 +56,34 @@ __host__ __device__ __forceinline__ void policy_features(float* f, uint64_t nF, 
 
 // Forward pass by one full warp: lane j owns hidden unit j of both layers.
 // Returns the 4 outputs in lanes 0..3 (broadcast to every lane via out[]).
+// `w` may point to global or shared memory (plain loads only).
 __device__ __forceinline__ void policy_forward_warp(const float* __restrict__ w, const float* f, float* out) {
   const int lane = threadIdx.x & 31;
-  float h1 = __ldg(&w[kPolOffB1 + lane]);
+  float h1 = w[kPolOffB1 + lane];
 #pragma unroll
-  for (int i = 0; i < kPolFeat; ++i) h1 = fmaf(f[i], __ldg(&w[kPolOffW1 + i * kPolHidden + lane]), h1);
+  for (int i = 0; i < kPolFeat; ++i) h1 = fmaf(f[i], w[kPolOffW1 + i * kPolHidden + lane], h1);
   h1 = fmaxf(h1, 0.0f);
-  float h2 = __ldg(&w[kPolOffB2 + lane]);
+  float h2 = w[kPolOffB2 + lane];
 #pragma unroll
   for (int i = 0; i < kPolHidden; ++i)
-    h2 = fmaf(__shfl_sync(0xFFFFFFFFu, h1, i), __ldg(&w[kPolOffW2 + i * kPolHidden + lane]), h2);
+    h2 = fmaf(__shfl_sync(0xFFFFFFFFu, h1, i), w[kPolOffW2 + i * kPolHidden + lane], h2);
   h2 = fmaxf(h2, 0.0f);
 #pragma unroll
   for (int a = 0; a < kPolArms; ++a) {
-    float y = h2 * __ldg(&w[kPolOffW3 + lane * kPolArms + a]);
+    float y = h2 * w[kPolOffW3 + lane * kPolArms + a];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(0xFFFFFFFFu, y, o);
-    out[a] = y + __ldg(&w[kPolOffB3 + a]);
+    out[a] = y + w[kPolOffB3 + a];
   }
 }
 
 // Arm with the smallest prediction among the allowed ones (lowest index on
-// ties); arm 0 if any allowed prediction is not finite.
+// ties), kept only if it beats arm 0 (the paper's IN+OUT on the sparse queue)
+// by kPolicyMargin in log2 time per settled vertex -- the network was fitted on
+// smaller graphs, and a switch it is unsure of tends to cost more than it
+// saves; arm 0 if any allowed prediction is not finite.
+constexpr float kPolicyMargin = 0.35f;
+
 __device__ __forceinline__ int policy_pick(const float* y, bool allow_simple) {
   const int na = allow_simple ? 4 : 2;
   int best = 0;
@@ -84,7 +91,7 @@ __device__ __forceinline__ int policy_pick(const float* y, bool allow_simple) {
     if (!isfinite(y[a])) return 0;
     if (y[a] < y[best]) best = a;
   }
-  return best;
+  return y[best] < y[0] - kPolicyMargin ? best : 0;
 }
 
 }  // namespace sssp

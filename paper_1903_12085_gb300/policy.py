@@ -99,9 +99,10 @@ def training_cases(shrink_base: int = 0):
     import graphgen as gg
 
     wls = [gg.workload(1), gg.workload(1, shrink=1), gg.workload(3, shrink=8 + shrink_base),
-           gg.workload(3, shrink=10 + shrink_base), gg.workload(5, shrink=8 + shrink_base),
-           gg.workload(5, shrink=10 + shrink_base), gg.workload(2, shrink=6 + shrink_base),
-           gg.workload(2, shrink=8 + shrink_base)]
+           gg.workload(3, shrink=10 + shrink_base), gg.workload(5, shrink=5 + shrink_base),
+           gg.workload(5, shrink=6 + shrink_base),
+           gg.workload(5, shrink=8 + shrink_base), gg.workload(5, shrink=10 + shrink_base),
+           gg.workload(2, shrink=6 + shrink_base), gg.workload(2, shrink=8 + shrink_base)]
     cases = []
     for wl in wls:
         gi, s = wl.solves[0]

@@ -29,11 +29,13 @@ TUNINGS = {
     "solo_edges_3blk": dict(solo_max_frontier=4096, grid_blocks=3, solo_max_edges=24),
     "one_block": dict(solo_max_frontier=0, grid_blocks=1, solo_max_edges=0),
     "one_block_solo": dict(solo_max_frontier=4096, grid_blocks=1, solo_max_edges=1 << 30),
-    "nearfar_grid_3blk": dict(solo_max_frontier=0, grid_blocks=3, nearfar_min_frontier=4, nearfar_target=6),
+    "nearfar_grid_3blk": dict(solo_max_frontier=0, grid_blocks=3, nearfar_min_frontier=4, nearfar_target=6,
+                              nearfar_min_share=0),
     "nearfar_solo_3blk": dict(solo_max_frontier=4096, grid_blocks=3, solo_max_edges=64,
-                              nearfar_min_frontier=8, nearfar_target=40),
-    "nearfar_one_block": dict(solo_max_frontier=0, grid_blocks=1, nearfar_min_frontier=1, nearfar_target=1),
-    "nearfar_auto_target": dict(nearfar_min_frontier=256, nearfar_target=0),
+                              nearfar_min_frontier=8, nearfar_target=40, nearfar_min_share=0),
+    "nearfar_one_block": dict(solo_max_frontier=0, grid_blocks=1, nearfar_min_frontier=1, nearfar_target=1,
+                              nearfar_min_share=0),
+    "nearfar_auto_target": dict(nearfar_min_frontier=256, nearfar_target=0, nearfar_min_share=8),
 }
 
 

@@ -143,8 +143,13 @@ def test_trained_policy_gain(capsys):
     w, hist = pol.fit_and_load()
     assert hist[-1][1] < hist[0][1]  # training lowers the loss
     rows = []
-    for k, shrink in [(3, 4), (5, 4), (1, 0), (2, 4)]:
-        wl = gg.workload(k, shrink=shrink)
+    # held out: none of these graphs is among the training graphs (the third
+    # has the first workload's shape, drawn with another seed)
+    held_out = [gg.workload(3, shrink=4), gg.workload(5, shrink=4),
+                gg.Workload("gnm_n16384_m131072_seed2", [gg.gnm(16384, 131072, 0, 1 << 24, gg.SEED_BASE + 101)],
+                            [(0, 0)]),
+                gg.workload(2, shrink=4)]
+    for wl in held_out:
         gi, s = wl.solves[0]
         G = sp.Graph.from_csr(wl.graphs[gi], reverse=True)
         t_fix, p_fix = _time(G, s, sp.IN_OUT)
