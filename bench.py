@@ -254,8 +254,11 @@ def main():
     batched = args.workload == 4
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda")
 
+    batch_tune = None
     if batched:
         B = sp.Batch([G[i] for i, _ in wl.solves], [s for _, s in wl.solves], crit)
+        bpg, _ = B.autotune()
+        batch_tune = {"blocks_per_solve": bpg}
         edges_per_step = None
 
         def step(k):
@@ -369,6 +372,9 @@ def main():
         rng_src = [int(gg.splitmix64_nth(0x5EED0B, i) >> 32) * g0.n >> 32 for i in range(args.batch_sources)]
         rng_src[0] = wl.solves[0][1]
         B = sp.Batch([G[gi0]] * len(rng_src), rng_src, crit)
+        t0 = time.perf_counter()
+        bpg, tuned_ms = B.autotune()  # the library's autotuner picks blocks per solve
+        tune_s = time.perf_counter() - t0
         for _ in range(args.warmup):
             B.launch()
         torch.cuda.synchronize()
@@ -386,7 +392,8 @@ def main():
             pg.barrier()
         bms_local = sum(a.elapsed_time(b) for a, b in bev) / args.steps
         bms, btot = combine_ranks(pg, "cuda", bms_local, {"edges": bedges, "sources": len(rng_src)})
-        batched_leg = {"sources": len(rng_src), "ms_per_launch": bms,
+        batched_leg = {"sources": len(rng_src), "ms_per_launch": bms, "blocks_per_solve": bpg,
+                       "autotune_s": round(tune_s, 2),
                        "queries_per_s": btot["sources"] / (bms * 1e-3),
                        "value": btot["edges"] / (bms * 1e-3) / 1e9, "unit": "GTEPS",
                        "speedup_queries_vs_single": (len(rng_src) / bms_local) / (nsolves / local_ms)}
@@ -433,7 +440,7 @@ def main():
                        "queries_per_s": tot["solves"] / (total_ms * 1e-3),
                        "us_per_phase": 1e3 * local_ms / phases, "sum_frontier_per_solve": tot["sum_f"] / tot["solves"],
                        "prep_ms": prep_ms, "l2": "flushed between steps (2x L2 buffer written)",
-                       "parallelism": f"replicas x{ws}"},
+                       "parallelism": f"replicas x{ws}", "batch_autotune": batch_tune},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "learned_policy": learned, "batched": batched_leg,
             "gpu_launches": args.steps, "clocks": clocks,

@@ -193,6 +193,15 @@ sssp_status sssp_batch_create(sssp_graph* const* graphs, const uint32_t* sources
 sssp_status sssp_batch_launch(sssp_batch* b, void* stream);
 void sssp_batch_destroy(sssp_batch* b);
 
+/* Autotuner of a prepared batch: runs the batch with every candidate number
+ * of blocks per solve (1, 2, 4, ... and all co-resident blocks), each once to
+ * warm up and once timed with CUDA events on `stream`, keeps the fastest and
+ * re-captures the CUDA graph with it.  Results never depend on the choice (the
+ * outputs hold the last run's, identical to any other run's).  bpg_out and
+ * ms_out (either may be NULL) get the chosen value and its launch time.
+ * Synchronous.  A library feature with no counterpart in the paper. */
+sssp_status sssp_batch_autotune(sssp_batch* b, void* stream, uint32_t* bpg_out, float* ms_out);
+
 /* ---- per-phase policy network ------------------------------------------
  * With SSSP_POLICY_LEARNED (criterion bits must be IN_STATIC | OUT_STATIC, the
  * fallback arm) every phase picks one of four arms:
@@ -205,7 +214,10 @@ void sssp_batch_destroy(sssp_batch* b);
  * (arm field: bit 0 dense, bit 1 single-block, bit 7 policy, bits 8..15 index).
  * Network: W1[8][32] b1[32] W2[32][32] b2[32] W3[32][4] b3[4] (float32,
  * input index first, ReLU after both hidden layers); outputs are predicted
- * log2(phase time / settled vertices) per arm and the smallest one wins.
+ * log2(phase time / settled vertices) per arm; the smallest one wins if it
+ * is below arm 0's by a margin of 0.35, else arm 0 runs.  While the fringe is
+ * split into near and far parts (sssp_tuning's nearfar fields) every phase
+ * runs arm 0, whose sparse queue is then the near part.
  * Features (sssp_policy_features computes them on the host):
  *   log2(1+|F|)/24, |F|/n, log2(1+E')/24, log2(1+S')/24, log2(1+k)/16,
  *   log2(n)/32, (m/n)/32, S'/(1+F')
@@ -289,7 +301,7 @@ sssp_status sssp_solve_noalloc(uint32_t n, uint64_t m, const uint64_t* row_offse
  * 256ths of n (a refill scans all n vertex records, which pays off only for a
  * fringe that is a sizeable share of the graph; 0 = no such condition).
  * Applies to launches made after the call; sssp_set_tuning(NULL) restores the
- * defaults (4096, 0, 0, 2048, 65536, 0, 32). */
+  * defaults (4096, 0, 0, 2048, 1048576, 0, 32). */
 typedef struct {
   uint32_t solo_max_frontier;
   uint32_t batch_blocks_per_solve;

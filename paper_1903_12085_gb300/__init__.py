@@ -80,6 +80,7 @@ def lib():
             "sssp_set_wait_limit_ns": [u64],
             "sssp_selftest_wait": [u64],
             "sssp_solve_noalloc": [u32, u64, p, p, u32, u32, p, p, p],
+            "sssp_batch_autotune": [p, p, p, p],
             "sssp_set_tuning": [p],
             "sssp_get_tuning": [p],
             "sssp_policy_load": [p, ctypes.c_size_t],
@@ -365,6 +366,14 @@ class Batch:
 
     def launch(self, stream=None):
         _check(lib().sssp_batch_launch(self.handle, _stream_ptr(stream)))
+
+    def autotune(self, stream=None):
+        """sssp_batch_autotune: time every blocks-per-solve candidate, keep the
+        fastest; returns (blocks per solve, ms per launch)."""
+        bpg = ctypes.c_uint32()
+        ms = ctypes.c_float()
+        _check(lib().sssp_batch_autotune(self.handle, _stream_ptr(stream), ctypes.byref(bpg), ctypes.byref(ms)))
+        return bpg.value, ms.value
 
     def close(self):
         if getattr(self, "handle", None):

@@ -198,18 +198,26 @@ __device__ __forceinline__ const float* policy_smem() {
   return reinterpret_cast<const float*>(smem_all + kPolicySmemOffset);
 }
 
-// allow_simple = false restricts the choice to the IN-STATIC arms (while the
-// fringe is split into near and far parts).
+// split = true (the fringe is split into near and far parts) fixes arm 0,
+// IN-STATIC on the sparse queue: the split exists for large fringes, where the
+// queue scan is what it saves, and IN-SIMPLE cannot use its static keys.
 // nQ: queue length (the dense/sparse choice without a policy); nF: |F|.
 __device__ Arm choose_arm(const SolveParams& p, uint64_t k, uint32_t nQ, uint32_t nF, uint64_t e_prev,
-                          uint64_t s_prev, uint64_t f_prev, bool allow_simple) {
+                          uint64_t s_prev, uint64_t f_prev, bool split) {
   if (!(p.crit & SSSP_POLICY_LEARNED) || p.policy == nullptr) return arm_for(p, nQ);
+  if (split) {
+    Arm a;
+    a.in_simple = false;
+    a.dense = false;
+    a.index = 0;
+    return a;
+  }
   __shared__ int s_arm;
   if ((threadIdx.x >> 5) == 0) {
     float f[kPolFeat], y[kPolArms];
     policy_features(f, nF, p.g.n, p.g.m, k, e_prev, s_prev, f_prev);
     policy_forward_warp(policy_smem(), f, y);
-    if (threadIdx.x == 0) s_arm = policy_pick(y, allow_simple && p.ws.cur_in != nullptr);
+    if (threadIdx.x == 0) s_arm = policy_pick(y, p.ws.cur_in != nullptr);
   }
   __syncthreads();
   Arm a;
@@ -632,7 +640,7 @@ __device__ __forceinline__ bool run_phase(const SolveParams& p, const Grp& grp, 
   const uint32_t nQ = ldcg_u32(&p.ws.ctl->slot[k % 4].qcount);
   const uint32_t nF = nQ + (md.nearfar ? ldcg_u32(&p.ws.ctl->far_count) : 0u);
   const Arm arm = choose_arm(p, k, nQ, nF, (uint32_t)ldcg_u64(&prev->relax_packed), ldcg_u32(&prev->settled_now),
-                             ldcg_u32(&prev->fsize), bound == kNoBound);
+                             ldcg_u32(&prev->fsize), bound != kNoBound);
   if (grp.rank == 0 && threadIdx.x == 0) p.ws.ctl->slot[k % 4].arm = arm_code(arm, grp.size == 1) | nf_code;
   if (!phase_select(p, grp, md, arm, k, sh, st)) return false;
   return bound != kNoBound ? phase_relax<true>(p, grp, md, arm, k, bound, false, sh, st)
@@ -746,10 +754,10 @@ __device__ uint64_t solo_episode(const SolveParams& p, const Mode& md, uint64_t 
     const uint32_t* sq = cur ? sqb : sqa;
     uint32_t* sqn = cur ? sqa : sqb;
     uint32_t* gqn = w.q[cur ^ 1];
-    // the policy is evaluated on the first phase of the episode and every 4th
+    // the policy is evaluated on the first phase of the episode and every 8th
     // phase after it (the choice is logged per phase either way)
-    if (since_pick == 0) arm = choose_arm(p, k, nF, nF + far, e_prev, s_prev, f_prev, !kNF);
-    since_pick = (since_pick + 1) & 3u;
+    if (since_pick == 0) arm = choose_arm(p, k, nF, nF + far, e_prev, s_prev, f_prev, kNF);
+    since_pick = (since_pick + 1) & 7u;
     const bool in_dyn = md.use_in && arm.in_simple && w.cur_in != nullptr;
     const uint32_t fs = nF + far;  // |F| at the start of the phase
     unsigned long long t0 = 0, t_sel = 0;
@@ -1403,19 +1411,11 @@ __device__ void solve_body(const SolveParams& p, const Grp& grp, unsigned char* 
         }
       } else if (far == 0 && bound == kNoBound && nF >= p.nf_min &&
                  (uint64_t)nF * 256 >= (uint64_t)p.nf_share * n) {
-        // with a policy, the split is its choice too: only when it picks an
-        // IN-STATIC arm for this phase (the split then keeps it to those)
-        bool split = true;
-        if ((p.crit & SSSP_POLICY_LEARNED) && p.policy) {
-          const PhaseSlot* prev = &ctl->slot[(k + 3) % 4];
-          split = choose_arm(p, k, nF, nF, (uint32_t)ldcg_u64(&prev->relax_packed), ldcg_u32(&prev->settled_now),
-                             ldcg_u32(&prev->fsize), true).index < 2;
-        }
-        if (split) {
-          if (!nf_split(p, grp, md, k, sh, bound, nf_uses)) return;
-          nF = ldcg_u32(&ctl->slot[k % 4].qcount);
-          if (bound != kNoBound) nf_code = kArmNfRefill;
-        }
+        // (with a policy too: while the fringe is split, every phase runs
+        // the static sparse arm, see choose_arm)
+        if (!nf_split(p, grp, md, k, sh, bound, nf_uses)) return;
+        nF = ldcg_u32(&ctl->slot[k % 4].qcount);
+        if (bound != kNoBound) nf_code = kArmNfRefill;
       }
       if (bound != kNoBound) nf_code |= kArmNfActive;
     } else if (nF == 0) {
@@ -1759,6 +1759,7 @@ struct BatchPlan {
   uint32_t crit = 0;
   uint32_t bpg = 1;                    // blocks per solve
   uint32_t groups = 0;
+  uint32_t max_groups = 0;             // gslots allocated (any bpg >= 1 fits)
   BatchItem* items = nullptr;          // device, largest graph first
   unsigned int* next = nullptr;        // device work counter
   GroupSlot* gslots = nullptr;         // device, one per group
@@ -1830,6 +1831,7 @@ sssp_status batch_build(sssp_graph* const* graphs, const uint32_t* sources, uint
   b->crit = crit;
   b->bpg = bpg;
   b->groups = std::max<uint32_t>(1, std::min<uint32_t>(count, resident / bpg));
+  b->max_groups = std::max<uint32_t>(1, std::min(count, resident));
   // Largest solves first, so the tail of the queue holds the short ones.
   std::vector<uint32_t> order(count);
   for (uint32_t i = 0; i < count; ++i) order[i] = i;
@@ -1852,7 +1854,7 @@ sssp_status batch_build(sssp_graph* const* graphs, const uint32_t* sources, uint
   }
   if (cudaMalloc(&b->items, count * sizeof(BatchItem)) != cudaSuccess ||
       cudaMalloc(&b->next, sizeof(unsigned int)) != cudaSuccess ||
-      cudaMalloc(&b->gslots, b->groups * sizeof(GroupSlot)) != cudaSuccess ||
+      cudaMalloc(&b->gslots, std::max<uint32_t>(1, std::min(count, resident)) * sizeof(GroupSlot)) != cudaSuccess ||
       cudaMalloc(&b->err, sizeof(int)) != cudaSuccess) {
     batch_free(b);
     return fail(SSSP_ERR_OUT_OF_MEMORY, "device allocation failed");
@@ -1872,6 +1874,24 @@ sssp_status batch_build(sssp_graph* const* graphs, const uint32_t* sources, uint
     return fail(SSSP_ERR_CUDA, "copy of batch descriptors failed");
   }
   *out = b;
+  return SSSP_OK;
+}
+
+// Capture the batch's launch (current blocks per solve) in a CUDA graph.
+sssp_status batch_capture(sssp_batch* b) {
+  cudaStream_t cap = nullptr;
+  if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess)
+    return fail(SSSP_ERR_CUDA, "stream creation failed");
+  sssp_status s = SSSP_OK;
+  cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    s = batch_enqueue(b, cap);
+    e = cudaStreamEndCapture(cap, &b->graph);
+  }
+  if (e == cudaSuccess && s == SSSP_OK) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+  cudaStreamDestroy(cap);
+  if (s != SSSP_OK) return s;
+  if (e != cudaSuccess) return fail(SSSP_ERR_CUDA, "CUDA graph capture failed: %s", cudaGetErrorString(e));
   return SSSP_OK;
 }
 
@@ -1953,23 +1973,60 @@ extern "C" sssp_status sssp_batch_create(sssp_graph* const* graphs, const uint32
   const uint32_t bpg = batch_blocks_per_solve() ? batch_blocks_per_solve() : choose_bpg(graphs, count);
   s = batch_build(graphs, sources, count, criterion, dist_out, phases_out, bpg, st, &b);
   if (s != SSSP_OK) return s;
-  cudaStream_t cap = nullptr;
-  if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) {
+  if ((s = batch_capture(b)) != SSSP_OK) {
     batch_free(b);
-    return fail(SSSP_ERR_CUDA, "stream creation failed");
-  }
-  cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
-  if (e == cudaSuccess) {
-    s = batch_enqueue(b, cap);
-    e = cudaStreamEndCapture(cap, &b->graph);
-  }
-  if (e == cudaSuccess && s == SSSP_OK) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
-  cudaStreamDestroy(cap);
-  if (e != cudaSuccess || s != SSSP_OK) {
-    batch_free(b);
-    return s != SSSP_OK ? s : fail(SSSP_ERR_CUDA, "CUDA graph capture failed: %s", cudaGetErrorString(e));
+    return s;
   }
   *out = b;
+  return SSSP_OK;
+}
+
+extern "C" sssp_status sssp_batch_autotune(sssp_batch* b, void* stream, uint32_t* bpg_out, float* ms_out) {
+  clear_error();
+  if (!b) return fail(SSSP_ERR_INVALID_ARG, "batch is NULL");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const uint32_t resident = (uint32_t)(g_blocks_per_sm * sm_count());
+  // candidates: powers of two and the full grid, each timed after a warm-up run
+  std::vector<uint32_t> cand;
+  for (uint32_t c = 1; c < resident; c *= 2) cand.push_back(c);
+  cand.push_back(resident);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  SSSP_CUDA_TRY(cudaEventCreate(&e0));
+  SSSP_CUDA_TRY(cudaEventCreate(&e1));
+  const uint32_t bpg0 = b->bpg;
+  uint32_t best = bpg0;
+  float best_ms = -1.0f;
+  sssp_status s = SSSP_OK;
+  for (uint32_t c : cand) {
+    b->bpg = c;
+    b->groups = std::max<uint32_t>(1, std::min<uint32_t>(b->count, resident / c));
+    if ((s = batch_enqueue(b, st)) != SSSP_OK) break;  // warm-up
+    if (cudaEventRecord(e0, st) != cudaSuccess || (s = batch_enqueue(b, st)) != SSSP_OK ||
+        cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+      if (s == SSSP_OK) s = fail(SSSP_ERR_CUDA, "timing a batch launch failed");
+      break;
+    }
+    if ((s = batch_status(b)) != SSSP_OK) break;
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (best_ms < 0.0f || ms < best_ms) {
+      best_ms = ms;
+      best = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->bpg = s == SSSP_OK ? best : bpg0;
+  b->groups = std::max<uint32_t>(1, std::min<uint32_t>(b->count, resident / b->bpg));
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+  const sssp_status sc = batch_capture(b);
+  if (s != SSSP_OK) return s;
+  if (sc != SSSP_OK) return sc;
+  if (bpg_out) *bpg_out = best;
+  if (ms_out) *ms_out = best_ms;
   return SSSP_OK;
 }
 

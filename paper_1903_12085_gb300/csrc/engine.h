@@ -14,7 +14,7 @@ constexpr int kTile = kThreads * kRelaxItems;
 constexpr uint32_t kSoloCap = 4096;
 constexpr uint32_t kSoloMaxDefault = kSoloCap;     // fringe size limit
 constexpr uint32_t kSoloEdgesDefault = 2048;       // relax edges above which a solo phase hands off
-constexpr uint32_t kNearFarMinDefault = 65536;     // fringe size at which the near/far split starts
+constexpr uint32_t kNearFarMinDefault = 1u << 20;   // fringe size at which the near/far split starts
 constexpr uint32_t kNearFarShareDefault = 32;      // ... and fringe share of n, in 256ths
 constexpr size_t kGridSmem = 66 * sizeof(unsigned long long)                               // reduction scratch, bases
                              + kTile * (2 * sizeof(uint32_t) + sizeof(unsigned long long))  // relax tile

@@ -13,8 +13,9 @@
 // phase-start state to 4 outputs, the predicted log2 of the phase time per
 // settled vertex for each arm; the phase takes the arm with the smallest
 // prediction if it beats arm 0 by a margin, else arm 0, the paper's IN+OUT
-// (IN-SIMPLE arms only when the in-edge CSR exists and the fringe is not split
-// into near and far parts; a non-finite prediction falls back to arm 0).
+// (IN-SIMPLE arms only when the in-edge CSR exists; a non-finite prediction
+// falls back to arm 0; while the engine keeps the fringe split into near and
+// far parts, every phase takes arm 0 without asking the network).
 //
 // Features (float32, all cheap and identical in every block):
 //   f0 = log2(1 + |F|) / 24          f4 = log2(1 + k) / 16     (k = phase index)

@@ -94,11 +94,13 @@ def train(X, T, A, epochs: int = 2000, lr: float = 1e-2, seed: int = 0, log_ever
 
 
 def training_cases(shrink_base: int = 0):
-    """Seeded training graphs of every family, smaller than the benchmark ones:
-    uniform G(n,m), R-MAT and grids (sources from their own recipes)."""
+    """Seeded training graphs of every family, none of them a benchmark or
+    held-out test graph: uniform G(n,m) from 2^13 to 2^22 vertices, R-MAT from
+    scale 12 to 20 and grids (sources from their own recipes)."""
     import graphgen as gg
 
-    wls = [gg.workload(1), gg.workload(1, shrink=1), gg.workload(3, shrink=8 + shrink_base),
+    wls = [gg.workload(1), gg.workload(1, shrink=1), gg.workload(3, shrink=2 + shrink_base),
+           gg.workload(5, shrink=2 + shrink_base), gg.workload(3, shrink=8 + shrink_base),
            gg.workload(3, shrink=10 + shrink_base), gg.workload(5, shrink=5 + shrink_base),
            gg.workload(5, shrink=6 + shrink_base),
            gg.workload(5, shrink=8 + shrink_base), gg.workload(5, shrink=10 + shrink_base),

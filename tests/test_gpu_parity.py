@@ -315,6 +315,26 @@ def test_prepared_batch_replays():
     B.close()
 
 
+def test_batch_autotune_keeps_results():
+    """The autotuner times every blocks-per-solve candidate and re-captures the
+    launch with the fastest; the replayed batch still gives the oracle's output."""
+    wl = gg.workload(4, shrink=5)
+    Gs = [sp.Graph.from_csr(g) for g in wl.graphs]
+    B = sp.Batch([Gs[i] for i, _ in wl.solves], [s for _, s in wl.solves], sp.IN_OUT)
+    bpg, ms = B.autotune()
+    assert ms > 0 and bpg >= 1 and (bpg & (bpg - 1) == 0 or bpg >= 128)
+    for o in B.outs:
+        o.fill_(0)
+    B.launch()
+    torch.cuda.synchronize()
+    ph = B.phases.cpu().numpy()
+    for k, (i, s) in enumerate(wl.solves):
+        g = wl.graphs[i]
+        assert (sp.as_uint64(B.outs[k]) == oracle.dijkstra(g, s)).all()
+        assert ph[k] == oracle.simulate(g, s, sp.IN_OUT).phases
+    B.close()
+
+
 @pytest.mark.parametrize("crit", [sp.IN_OUT, sp.IN_STATIC, sp.OUT_STATIC], ids=["in_out", "in", "out"])
 def test_nearfar_split_runs_and_changes_nothing(crit):
     """With a small split threshold the fringe is split and refilled many times
