@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", type=int, default=DEFAULT_WORKLOAD)
+    ap.add_argument("--shrink", type=int, default=0,
+                    help="a smaller member of the workload's family (sizes / 2^shrink), for profiling captures")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--criterion", default="in_out", choices=["in_out", "simple", "learned"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -59,7 +61,7 @@ def parse():
 # workload name and criterion, with a hash of the engine sources the capture ran
 # on: once the kernel changes the figure no longer applies and is reported null.
 MEASURED_TRAFFIC = {
-    ("grid_1024x1024", "in_out"): (51744256 + 3729152, "efc9c87bd754b90d"),
+    ("grid_1024x1024", "in_out"): (52034560 + 8113664, "9244790d4936733f"),
 }
 ENGINE_SOURCES = ("engine.cu", "engine.h", "common.cuh", "policy.cuh")
 
@@ -170,9 +172,9 @@ def rank_solve(solves: list, rank: int, k: int):
     return solves[(k + rank) % len(solves)]
 
 
-def build_workload(k: int):
+def build_workload(k: int, shrink: int = 0):
     import graphgen as gg
-    return gg.workload(k)
+    return gg.workload(k, shrink=shrink)
 
 
 def crit_value(sp, name):
@@ -228,7 +230,7 @@ def cpu_baseline(wl, budget_s=12.0):
 def main():
     args = parse()
     ws, rank, local = dist_env()
-    wl = build_workload(args.workload)
+    wl = build_workload(args.workload, args.shrink)
     if args.impl == "reference":
         run_reference(args, wl)
         return
@@ -272,10 +274,13 @@ def main():
 
     # edges / phases / frontier work per step (deterministic: from one traced
     # pass per solve), indexed like step(k)
+    # (the trace gives the queue entries each phase scanned: with the near/far
+    # split the far part of F is not touched)
     per_solve = []
     for k in range(len(wl.solves)):
         gi, s = rank_solve(wl.solves, rank, k)
-        _, stats, _, _ = sp.solve_trace(G[gi], s, crit, settle=False)
+        _, stats, _, tr = sp.solve_trace(G[gi], s, crit, settle=False, trace_cap=min(1 << 21, G[gi].n + 1))
+        stats["sum_queued"] = int(tr["queued"].astype(np.int64).sum())
         per_solve.append(stats)
     for k in range(args.warmup):
         step(k)
@@ -283,7 +288,7 @@ def main():
     if pg:
         pg.barrier()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    edges = phases = settled = sum_f = 0
+    edges = phases = settled = sum_f = sum_q = 0
     nsolves = 0
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
@@ -295,12 +300,12 @@ def main():
             if batched:
                 for st in per_solve:
                     edges += st["edges_relaxed"]; phases += st["phases"]
-                    settled += st["settled"]; sum_f += st["sum_frontier"]
+                    settled += st["settled"]; sum_f += st["sum_frontier"]; sum_q += st["sum_queued"]
                 nsolves += len(per_solve)
             else:
                 st = per_solve[k % len(per_solve)]
                 edges += st["edges_relaxed"]; phases += st["phases"]
-                settled += st["settled"]; sum_f += st["sum_frontier"]
+                settled += st["settled"]; sum_f += st["sum_frontier"]; sum_q += st["sum_queued"]
                 nsolves += 1
         torch.cuda.synchronize()
     if pg:
@@ -310,18 +315,22 @@ def main():
     local_edges = edges
     total_ms, tot = combine_ranks(pg, "cuda", local_ms,
                                   {"edges": edges, "phases": phases, "settled": settled,
-                                   "sum_f": sum_f, "solves": nsolves})
+                                   "sum_f": sum_f, "sum_q": sum_q, "solves": nsolves})
     value = tot["edges"] / (total_ms * 1e-3) / 1e9
     kernel_ms = local_ms / args.steps
 
     # roofline of the solve kernel: algorithmic bytes per launch / launch time
     # per solve: 16 B per relaxed edge (8 B edge + 8 B distance word) + 16 B per
-    # settled vertex + 16 B per frontier entry per phase
-    alg_bytes = (16 * local_edges + 16 * settled + 16 * sum_f) / args.steps
+    # settled vertex + 16 B per queue entry a phase scans (the paper's
+    # identification work, sum of |F| over phases, less the far part of F that
+    # the near/far split leaves untouched)
+    alg_bytes = (16 * local_edges + 16 * settled + 16 * sum_q) / args.steps
     achieved = alg_bytes / (kernel_ms * 1e-3) / 1e9
+    edge_only = 16 * local_edges / args.steps / (kernel_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": None if batched else measured_traffic(wl.name, args.criterion),
-                "peak_kind": peak_kind, "kernel": "k_solve_grid" if not batched else "k_solve_batch"}
+                "peak_kind": peak_kind, "kernel": "k_solve_grid" if not batched else "k_solve_batch",
+                "edge_only_frac": edge_only / hbm}
 
     # ---- learned per-phase policy (trained here on small graphs, by the
     # library's own FP32 kernels), same workload and timing rules
@@ -439,6 +448,7 @@ def main():
                        "phases_per_solve": tot["phases"] / tot["solves"],
                        "queries_per_s": tot["solves"] / (total_ms * 1e-3),
                        "us_per_phase": 1e3 * local_ms / phases, "sum_frontier_per_solve": tot["sum_f"] / tot["solves"],
+                       "sum_queued_per_solve": tot["sum_q"] / tot["solves"],
                        "prep_ms": prep_ms, "l2": "flushed between steps (2x L2 buffer written)",
                        "parallelism": f"replicas x{ws}", "batch_autotune": batch_tune},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,

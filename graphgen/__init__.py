@@ -125,10 +125,11 @@ def _thr(p: float) -> int:
 
 
 def rmat(scale: int, edge_factor: int, a: float, b: float, c: float, wlo: int, whi: int,
-         seed: int, name: str = "") -> Graph:
-    """R-MAT graph with 2^scale vertices and edge_factor * 2^scale edges."""
+         seed: int, name: str = "", m: int | None = None) -> Graph:
+    """R-MAT graph with 2^scale vertices and edge_factor * 2^scale edges (or
+    exactly m edges when m is given)."""
     n = 1 << scale
-    m = edge_factor * n
+    m = edge_factor * n if m is None else int(m)
     row_off = np.empty(n + 1, np.uint64)
     col = np.empty(m, np.uint32)
     w = np.empty(m, np.uint32)
