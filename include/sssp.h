@@ -55,16 +55,25 @@ typedef enum {
  *   SSSP_OUT_STATIC  d[v] <= min_{u in F} (d[u] + min_{(u,w) in E} c(u,w)) (eq. crit:outstatic)
  *   SSSP_IN_SIMPLE   as IN_STATIC, minimum over in-edges from unsettled w  (eq. crit:insimple)
  *   SSSP_OUT_SIMPLE  as OUT_STATIC, minimum over out-edges to unsettled w  (eq. crit:outsimple)
+ *   SSSP_IN_FULL     d[v] <= minD + min over in-edges (w,v), w unsettled, of
+ *                    c(w,v) for w in F and c(w,v) + min_{(x,w) in E} c(x,w)
+ *                    for w unexplored (eq. crit:in, with Proposition 1's
+ *                    precomputed minimum for unexplored w)
+ *   SSSP_OUT_WEAK    d[v] <= min_{u in F} (d[u] + min over out-edges (u,w), w
+ *                    unsettled, of c(u,w) for w in F and c(u,w) +
+ *                    min_{(w,x) in E} c(w,x) for w unexplored) (eq. crit:outweak)
  *   SSSP_DIJK        the single fringe vertex of minimum d, lowest id on ties (Section 3)
  * An empty minimum is infinite: the IN test then holds, and the vertex adds
- * nothing to the OUT threshold.  IN_SIMPLE needs a graph built with
- * SSSP_GRAPH_REVERSE.  "IN+OUT" = SSSP_IN_STATIC | SSSP_OUT_STATIC is the
+ * nothing to the OUT threshold.  IN_SIMPLE and IN_FULL need a graph built
+ * with SSSP_GRAPH_REVERSE.  "IN+OUT" = SSSP_IN_STATIC | SSSP_OUT_STATIC is the
  * criterion of the paper's implementation (Section 5). */
 enum {
   SSSP_IN_STATIC = 1u << 0,
   SSSP_OUT_STATIC = 1u << 1,
   SSSP_IN_SIMPLE = 1u << 2,
   SSSP_OUT_SIMPLE = 1u << 3,
+  SSSP_IN_FULL = 1u << 4,
+  SSSP_OUT_WEAK = 1u << 5,
   SSSP_DIJK = 1u << 6,
   SSSP_CRITERIA_MASK = 0xFFFFu,
   /* Execution options (do not change results, only speed). */
@@ -194,9 +203,11 @@ sssp_status sssp_batch_launch(sssp_batch* b, void* stream);
 void sssp_batch_destroy(sssp_batch* b);
 
 /* Autotuner of a prepared batch: runs the batch with every candidate number
- * of blocks per solve (1, 2, 4, ... and all co-resident blocks), each once to
- * warm up and once timed with CUDA events on `stream`, keeps the fastest and
- * re-captures the CUDA graph with it.  Results never depend on the choice (the
+ * of blocks per solve (the batch's own choice, 1, 2, 4, ... and all
+ * co-resident blocks), each once to warm up and three times timed with CUDA
+ * events on `stream`, keeps the candidate with the smallest median (another
+ * candidate must beat the batch's own choice by 3 %) and re-captures the CUDA
+ * graph with it.  Results never depend on the choice (the
  * outputs hold the last run's, identical to any other run's).  bpg_out and
  * ms_out (either may be NULL) get the chosen value and its launch time.
  * Synchronous.  A library feature with no counterpart in the paper. */
@@ -291,8 +302,9 @@ sssp_status sssp_solve_noalloc(uint32_t n, uint64_t m, const uint64_t* row_offse
  * chosen from the batch); grid_blocks: blocks of a single solve (0 = chosen
  * from n, capped at the co-resident maximum);
  * nearfar_min_frontier: with static criteria only (IN-STATIC and/or
- * OUT-STATIC, no policy) and n <= 2^30, a fringe of at least this many
- * vertices is split into a near part, kept in the queue that every phase
+ * OUT-STATIC) and n <= 2^30, a fringe of at least this many vertices per
+ * block working on the solve (all blocks of a single solve, the group of a
+ * batched one) is split into a near part, kept in the queue that every phase
  * scans, and a far part of vertices that no phase can settle before a bound B
  * on d(v) - inmin(v) is raised (0 = never split);
  * nearfar_target: vertices the near part is sized to when B is set or raised
@@ -301,7 +313,7 @@ sssp_status sssp_solve_noalloc(uint32_t n, uint64_t m, const uint64_t* row_offse
  * 256ths of n (a refill scans all n vertex records, which pays off only for a
  * fringe that is a sizeable share of the graph; 0 = no such condition).
  * Applies to launches made after the call; sssp_set_tuning(NULL) restores the
-  * defaults (4096, 0, 0, 2048, 1048576, 0, 32). */
+  * defaults (4096, 0, 0, 2048, 8192, 0, 32). */
 typedef struct {
   uint32_t solo_max_frontier;
   uint32_t batch_blocks_per_solve;

@@ -27,6 +27,8 @@ IN_STATIC = 1 << 0
 OUT_STATIC = 1 << 1
 IN_SIMPLE = 1 << 2
 OUT_SIMPLE = 1 << 3
+IN_FULL = 1 << 4
+OUT_WEAK = 1 << 5
 DIJK = 1 << 6
 POLICY_LEARNED = 1 << 16
 FRONTIER_DENSE = 1 << 17

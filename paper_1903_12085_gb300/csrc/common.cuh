@@ -123,6 +123,7 @@ struct SolveWS {
   uint32_t* cur_in;        // [n] in-row cursor (dynamic in-minimum), or nullptr
   uint32_t* im_dyn;        // [n] dynamic in-minimum of fringe vertices (IN-SIMPLE phases), or nullptr
   uint32_t* tile_owner;    // [m / tile + 2] relax-list entry holding each tile's first edge, or nullptr
+  unsigned long long* im_full;  // [n] IN (full) minima of fringe vertices (IN_FULL phases), or nullptr
   unsigned long long* dist;  // [n] output distances
   Ctl* ctl;
   uint32_t* settle_phase;  // [n] optional

@@ -124,6 +124,50 @@ __device__ __forceinline__ uint32_t in_min_dynamic(const GraphView& g, const Sol
   return cost;
 }
 
+// OUT-WEAK term of fringe vertex u on the phase-start state: the minimum over
+// out-edges (u,w) with w not settled of c(u,w) for w in F and c(u,w) +
+// outmin(w) for w unexplored (eq. crit:outweak).  A full scan of the row (the
+// term is not monotone: it drops when w enters F and grows when w settles).
+__device__ __forceinline__ unsigned long long out_min_weak(const GraphView& g, const SolveWS& w, uint32_t u) {
+  const uint64_t b = __ldg(&g.row_off[u]), e = __ldg(&g.row_off[u + 1]);
+  unsigned long long best = kInf64;
+  for (uint64_t c = b; c < e; ++c) {
+    const uint2 ed = __ldg(&g.edges[c]);
+    const uint8_t st = ldcg_u8(&w.status[ed.x]);
+    if (st == kS) continue;
+    unsigned long long x = ed.y;
+    if (st == kU) {
+      const uint32_t o = __ldg(&g.out_min[ed.x]);
+      if (o == kInf32) continue;  // no out-edge of w: no path through it
+      x += o;
+    }
+    best = x < best ? x : best;
+  }
+  return best;
+}
+
+// IN (full) term of fringe vertex v on the phase-start state: the minimum over
+// in-edges (w,v) with w not settled of c(w,v) for w in F and c(w,v) + inmin(w)
+// for w unexplored (eq. crit:in; an unexplored w has no settled in-neighbour,
+// so its static in-minimum is the one the criterion needs, Proposition 1).
+__device__ __forceinline__ unsigned long long in_min_full(const GraphView& g, const SolveWS& w, uint32_t v) {
+  const uint64_t b = __ldg(&g.rrow_off[v]), e = __ldg(&g.rrow_off[v + 1]);
+  unsigned long long best = kInf64;
+  for (uint64_t c = b; c < e; ++c) {
+    const uint2 ed = __ldg(&g.redges[c]);
+    const uint8_t st = ldcg_u8(&w.status[ed.x]);
+    if (st == kS) continue;
+    unsigned long long x = ed.y;
+    if (st == kU) {
+      const uint32_t i = __ldg(&g.in_min[ed.x]);
+      if (i == kInf32) continue;  // w is never reached: the term is infinite
+      x += i;
+    }
+    best = x < best ? x : best;
+  }
+  return best;
+}
+
 struct Shared {
   unsigned long long* red;    // 64
   unsigned long long* bases;  // 2: output offsets reserved by the block
@@ -152,6 +196,8 @@ struct Mode {
   bool use_in;       // some IN criterion
   bool use_out;
   bool out_dyn;      // OUT-SIMPLE (three-step kind)
+  bool out_weak;     // OUT-WEAK (three-step kind)
+  bool in_full;      // IN (full) (three-step kind)
   bool dijk;
   bool nearfar;      // the fringe may be split into a near queue and a far part
 };
@@ -162,12 +208,14 @@ struct Mode {
 __device__ __forceinline__ Mode mode_of(const SolveParams& p) {
   const uint32_t crit = p.crit;
   Mode m;
+  m.out_weak = (crit & SSSP_OUT_WEAK) != 0;
+  m.in_full = (crit & SSSP_IN_FULL) != 0 && p.ws.im_full != nullptr;
   m.out_dyn = (crit & SSSP_OUT_SIMPLE) != 0;
-  m.use_out = m.out_dyn || (crit & SSSP_OUT_STATIC) != 0;
+  m.use_out = m.out_dyn || m.out_weak || (crit & SSSP_OUT_STATIC) != 0;
   m.dijk = (crit & SSSP_DIJK) != 0;
-  m.fused = !m.out_dyn && !m.dijk;
+  m.fused = !m.out_dyn && !m.out_weak && !m.in_full && !m.dijk;
   const bool policy = (crit & SSSP_POLICY_LEARNED) != 0;
-  m.use_in = (crit & (SSSP_IN_STATIC | SSSP_IN_SIMPLE)) != 0 || policy;
+  m.use_in = (crit & (SSSP_IN_STATIC | SSSP_IN_SIMPLE | SSSP_IN_FULL)) != 0 || policy;
   m.nearfar = m.fused && !(crit & SSSP_IN_SIMPLE) && p.nf_min != 0 && p.g.n <= kNearFarMaxVertices;
   return m;
 }
@@ -364,14 +412,21 @@ __device__ bool phase_select(const SolveParams& p, const Grp& grp, const Mode& m
     auto visit = [&](uint32_t v) {
       const unsigned long long dv = ldcg_u64(&w.vrec[v].d);
       lmin_d = dv < lmin_d ? dv : lmin_d;
-      if (md.use_out) {
-        const uint32_t om = md.out_dyn ? out_min_dynamic(g, w, v) : __ldg(&g.out_min[v]);
-        if (om != kInf32) {
+      if (md.use_out) {  // the strongest OUT bit set gives the largest threshold
+        unsigned long long om;
+        if (md.out_weak) {
+          om = out_min_weak(g, w, v);
+        } else {
+          const uint32_t o = md.out_dyn ? out_min_dynamic(g, w, v) : __ldg(&g.out_min[v]);
+          om = o == kInf32 ? kInf64 : o;
+        }
+        if (om != kInf64) {
           const unsigned long long x = dv + om;
           lmin_out = x < lmin_out ? x : lmin_out;
         }
       }
-      if (in_dyn) w.im_dyn[v] = in_min_dynamic(g, w, v, false);
+      if (md.in_full) w.im_full[v] = in_min_full(g, w, v);
+      else if (in_dyn) w.im_dyn[v] = in_min_dynamic(g, w, v, false);
     };
     if (dense) {
       for (uint64_t v = gtid; v < n; v += gthreads)
@@ -444,8 +499,13 @@ __device__ bool phase_select(const SolveParams& p, const Grp& grp, const Mode& m
       const unsigned long long dv = rr[j].d;
       bool sel = false;
       if (md.use_in) {
-        const uint32_t im = in_dyn ? ldcg_u32(&w.im_dyn[v]) : rr[j].im;
-        sel = (im == kInf32) || dv <= minD + im;
+        if (md.in_full) {
+          const unsigned long long im = ldcg_u64(&w.im_full[v]);
+          sel = (im == kInf64) || dv <= minD + im;
+        } else {
+          const uint32_t im = in_dyn ? ldcg_u32(&w.im_dyn[v]) : rr[j].im;
+          sel = (im == kInf32) || dv <= minD + im;
+        }
       }
       if (!sel && md.use_out) sel = dv <= minOut;
       if (!sel && md.dijk) sel = (v == amin);
@@ -1409,7 +1469,7 @@ __device__ void solve_body(const SolveParams& p, const Grp& grp, unsigned char* 
           if (leader) atomicCAS(&ctl->err, 0, (int)SSSP_ERR_INTERNAL);
           break;
         }
-      } else if (far == 0 && bound == kNoBound && nF >= p.nf_min &&
+      } else if (far == 0 && bound == kNoBound && (uint64_t)nF >= (uint64_t)p.nf_min * grp.size &&
                  (uint64_t)nF * 256 >= (uint64_t)p.nf_share * n) {
         // (with a policy too: while the fringe is split, every phase runs
         // the static sparse arm, see choose_arm)
@@ -1577,8 +1637,8 @@ sssp_status ensure_kernel_attrs() {
 }
 
 sssp_status check_crit(const sssp_graph* g, uint32_t crit) {
-  const uint32_t known = SSSP_IN_STATIC | SSSP_OUT_STATIC | SSSP_IN_SIMPLE | SSSP_OUT_SIMPLE | SSSP_DIJK |
-                         SSSP_FRONTIER_DENSE | SSSP_FRONTIER_AUTO | SSSP_POLICY_LEARNED;
+  const uint32_t known = SSSP_IN_STATIC | SSSP_OUT_STATIC | SSSP_IN_SIMPLE | SSSP_OUT_SIMPLE | SSSP_IN_FULL |
+                         SSSP_OUT_WEAK | SSSP_DIJK | SSSP_FRONTIER_DENSE | SSSP_FRONTIER_AUTO | SSSP_POLICY_LEARNED;
   if ((crit & SSSP_CRITERIA_MASK) == 0) return fail(SSSP_ERR_INVALID_ARG, "criterion mask has no criterion bit");
   if (crit & ~known) return fail(SSSP_ERR_INVALID_ARG, "unknown criterion bits 0x%x", crit & ~known);
   if (crit & SSSP_POLICY_LEARNED) {
@@ -1586,8 +1646,8 @@ sssp_status check_crit(const sssp_graph* g, uint32_t crit) {
     if ((crit & SSSP_CRITERIA_MASK) != (SSSP_IN_STATIC | SSSP_OUT_STATIC))
       return fail(SSSP_ERR_INVALID_ARG, "SSSP_POLICY_LEARNED takes IN_STATIC | OUT_STATIC as its fallback arm");
   }
-  if ((crit & SSSP_IN_SIMPLE) && !g->rrow_off)
-    return fail(SSSP_ERR_UNSUPPORTED, "IN-SIMPLE needs a graph built with SSSP_GRAPH_REVERSE");
+  if ((crit & (SSSP_IN_SIMPLE | SSSP_IN_FULL)) && !g->rrow_off)
+    return fail(SSSP_ERR_UNSUPPORTED, "IN-SIMPLE and IN (full) need a graph built with SSSP_GRAPH_REVERSE");
   return SSSP_OK;
 }
 
@@ -1618,6 +1678,7 @@ void workspace_free(Workspace* ws) {
   cudaFree(ws->cur_in);
   cudaFree(ws->im_dyn);
   cudaFree(ws->tile_owner);
+  cudaFree(ws->im_full);
   cudaFree(ws->dist);
   cudaFree(ws->ctl);
   cudaFreeHost(ws->ctl_host);
@@ -1636,7 +1697,7 @@ sssp_status workspace_alloc(uint32_t n, uint64_t m, bool want_cursors, bool want
     return s;
   }
   if (want_cursors && ((s = dev_alloc(&ws->cur_out, n)) || (s = dev_alloc(&ws->cur_in, n)) ||
-                       (s = dev_alloc(&ws->im_dyn, n)))) {
+                       (s = dev_alloc(&ws->im_dyn, n)) || (s = dev_alloc(&ws->im_full, n)))) {
     workspace_free(ws);
     return s;
   }
@@ -1676,6 +1737,7 @@ SolveWS ws_view(Workspace* ws, unsigned long long* dist, uint32_t crit, bool has
   w.cur_in = ((crit & (SSSP_IN_SIMPLE | SSSP_POLICY_LEARNED)) && has_reverse) ? ws->cur_in : nullptr;
   w.im_dyn = w.cur_in ? ws->im_dyn : nullptr;
   w.tile_owner = ws->tile_owner;
+  w.im_full = ((crit & SSSP_IN_FULL) && has_reverse) ? ws->im_full : nullptr;
   w.ctl = ws->ctl;
   return w;
 }
@@ -1840,7 +1902,7 @@ sssp_status batch_build(sssp_graph* const* graphs, const uint32_t* sources, uint
   });
   std::vector<BatchItem> h(count);
   b->ws.assign(count, nullptr);
-  const bool cursors = (crit & (SSSP_IN_SIMPLE | SSSP_OUT_SIMPLE)) != 0;
+  const bool cursors = (crit & (SSSP_IN_SIMPLE | SSSP_OUT_SIMPLE | SSSP_IN_FULL)) != 0;
   for (uint32_t k = 0; k < count; ++k) {
     const uint32_t i = order[k];
     if ((s = workspace_alloc(graphs[i]->n, graphs[i]->m, cursors, false, &b->ws[k])) != SSSP_OK) {
@@ -1986,36 +2048,43 @@ extern "C" sssp_status sssp_batch_autotune(sssp_batch* b, void* stream, uint32_t
   if (!b) return fail(SSSP_ERR_INVALID_ARG, "batch is NULL");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const uint32_t resident = (uint32_t)(g_blocks_per_sm * sm_count());
-  // candidates: powers of two and the full grid, each timed after a warm-up run
-  std::vector<uint32_t> cand;
-  for (uint32_t c = 1; c < resident; c *= 2) cand.push_back(c);
-  cand.push_back(resident);
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  SSSP_CUDA_TRY(cudaEventCreate(&e0));
-  SSSP_CUDA_TRY(cudaEventCreate(&e1));
+  // candidates: the batch's own choice (first), powers of two and the full
+  // grid; each runs once to warm up and kTimed times, scored by the median
+  constexpr int kTimed = 3;
   const uint32_t bpg0 = b->bpg;
+  std::vector<uint32_t> cand{bpg0};
+  for (uint32_t c = 1; c < resident; c *= 2)
+    if (c != bpg0) cand.push_back(c);
+  if (resident != bpg0) cand.push_back(resident);
+  cudaEvent_t ev[kTimed + 1];
+  for (auto& e : ev) SSSP_CUDA_TRY(cudaEventCreate(&e));
   uint32_t best = bpg0;
-  float best_ms = -1.0f;
+  float best_ms = -1.0f, first_ms = -1.0f;
   sssp_status s = SSSP_OK;
   for (uint32_t c : cand) {
     b->bpg = c;
     b->groups = std::max<uint32_t>(1, std::min<uint32_t>(b->count, resident / c));
     if ((s = batch_enqueue(b, st)) != SSSP_OK) break;  // warm-up
-    if (cudaEventRecord(e0, st) != cudaSuccess || (s = batch_enqueue(b, st)) != SSSP_OK ||
-        cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
-      if (s == SSSP_OK) s = fail(SSSP_ERR_CUDA, "timing a batch launch failed");
-      break;
+    if (cudaEventRecord(ev[0], st) != cudaSuccess) s = fail(SSSP_ERR_CUDA, "timing a batch launch failed");
+    for (int r = 0; r < kTimed && s == SSSP_OK; ++r) {
+      if ((s = batch_enqueue(b, st)) == SSSP_OK && cudaEventRecord(ev[r + 1], st) != cudaSuccess)
+        s = fail(SSSP_ERR_CUDA, "timing a batch launch failed");
     }
-    if ((s = batch_status(b)) != SSSP_OK) break;
-    float ms = 0.0f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (best_ms < 0.0f || ms < best_ms) {
+    if (s == SSSP_OK && cudaEventSynchronize(ev[kTimed]) != cudaSuccess)
+      s = fail(SSSP_ERR_CUDA, "timing a batch launch failed");
+    if (s != SSSP_OK || (s = batch_status(b)) != SSSP_OK) break;
+    float t[kTimed];
+    for (int r = 0; r < kTimed; ++r) cudaEventElapsedTime(&t[r], ev[r], ev[r + 1]);
+    std::sort(t, t + kTimed);
+    const float ms = t[kTimed / 2];
+    if (first_ms < 0.0f) first_ms = ms;
+    // another candidate replaces the batch's own choice only if clearly faster
+    if (best_ms < 0.0f || (ms < best_ms && ms < 0.97f * first_ms)) {
       best_ms = ms;
       best = c;
     }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  for (auto& e : ev) cudaEventDestroy(e);
   b->bpg = s == SSSP_OK ? best : bpg0;
   b->groups = std::max<uint32_t>(1, std::min<uint32_t>(b->count, resident / b->bpg));
   if (b->exec) cudaGraphExecDestroy(b->exec);

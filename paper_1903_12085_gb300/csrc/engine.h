@@ -14,7 +14,7 @@ constexpr int kTile = kThreads * kRelaxItems;
 constexpr uint32_t kSoloCap = 4096;
 constexpr uint32_t kSoloMaxDefault = kSoloCap;     // fringe size limit
 constexpr uint32_t kSoloEdgesDefault = 2048;       // relax edges above which a solo phase hands off
-constexpr uint32_t kNearFarMinDefault = 1u << 20;   // fringe size at which the near/far split starts
+constexpr uint32_t kNearFarMinDefault = 8192;      // fringe size per block of the solve at which the near/far split starts
 constexpr uint32_t kNearFarShareDefault = 32;      // ... and fringe share of n, in 256ths
 constexpr size_t kGridSmem = 66 * sizeof(unsigned long long)                               // reduction scratch, bases
                              + kTile * (2 * sizeof(uint32_t) + sizeof(unsigned long long))  // relax tile
@@ -41,7 +41,7 @@ struct SolveParams {
   unsigned long long wait_ns;
   uint32_t solo_max;    // largest fringe run by one block alone (0 = never)
   uint32_t solo_edges;  // relax edges above which a solo phase hands off to the group
-  uint32_t nf_min;      // fringe size at which the near/far split starts (0 = never)
+  uint32_t nf_min;      // fringe size per block of the solve at which the near/far split starts (0 = never)
   uint32_t nf_target;   // near-part size aimed at when the bound is set (0 = automatic)
   uint32_t nf_share;    // the split also needs |F| >= nf_share * n / 256
   const float* policy;  // policy network weights (device) or nullptr

@@ -16,7 +16,8 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 CRITS = [sp.IN_STATIC, sp.OUT_STATIC, sp.IN_OUT, sp.IN_SIMPLE, sp.OUT_SIMPLE, sp.SIMPLE,
-         sp.IN_STATIC | sp.OUT_SIMPLE, sp.IN_SIMPLE | sp.OUT_STATIC]
+         sp.IN_STATIC | sp.OUT_SIMPLE, sp.IN_SIMPLE | sp.OUT_STATIC,
+         sp.IN_FULL, sp.OUT_WEAK, sp.IN_FULL | sp.OUT_WEAK, sp.IN_FULL | sp.OUT_STATIC]
 MODES = [0, sp.FRONTIER_DENSE, sp.FRONTIER_AUTO]
 
 
@@ -35,7 +36,7 @@ TUNINGS = {
                               nearfar_min_frontier=8, nearfar_target=40, nearfar_min_share=0),
     "nearfar_one_block": dict(solo_max_frontier=0, grid_blocks=1, nearfar_min_frontier=1, nearfar_target=1,
                               nearfar_min_share=0),
-    "nearfar_auto_target": dict(nearfar_min_frontier=256, nearfar_target=0, nearfar_min_share=8),
+    "nearfar_auto_target": dict(nearfar_min_frontier=32, nearfar_target=0, nearfar_min_share=8),
 }
 
 
@@ -80,7 +81,8 @@ def test_golden_examples_on_gpu():
         g = gg.from_edges(ex["n"], ex["edges"])
         G = sp.Graph.from_csr(g, reverse=True)
         for run in ex["runs"]:
-            if run["crit"] & ~(sp.IN_STATIC | sp.OUT_STATIC | sp.IN_SIMPLE | sp.OUT_SIMPLE | sp.DIJK):
+            if run["crit"] & ~(sp.IN_STATIC | sp.OUT_STATIC | sp.IN_SIMPLE | sp.OUT_SIMPLE | sp.IN_FULL |
+                               sp.OUT_WEAK | sp.DIJK):
                 continue
             dist, stats, settle, _ = sp.solve_trace(G, 0, run["crit"])
             assert sp.as_uint64(dist).tolist() == [int(x) for x in ex["dist"]], ex["name"]
@@ -120,7 +122,7 @@ def test_workload_shapes_small(tuning):
         G = sp.Graph.from_csr(g, reverse=True)
         for _, s in wl.solves[:2]:
             ref = oracle.dijkstra(g, s)
-            for crit in [sp.IN_OUT, sp.SIMPLE]:
+            for crit in [sp.IN_OUT, sp.SIMPLE, sp.IN_FULL | sp.OUT_WEAK]:
                 for mode in MODES:
                     check(g, G, s, crit, ref, mode)
 
