@@ -43,6 +43,13 @@ OUT_WEAK = 32
 DIJK = 64
 ORACLE = 128
 OUT_FULL = 256
+APPROX = 512  # approximate IN (full) / OUT-WEAK minima, recomputed every k-th phase
+
+
+def approx(k: int) -> int:
+    """Criterion bits of APPROX with recomputation every k-th phase (1..63)."""
+    assert 1 <= k <= 63
+    return APPROX | (k << 10)
 
 _ERRORS = {-1: "out of memory", -2: "bad argument", -3: "a phase selected no vertex (criterion not complete)",
            -4: "a selected vertex was not correct (criterion not sound)"}

@@ -36,6 +36,19 @@
  *   128 ORACLE      d[v] = dist(s,v), using the caller's reference distances
  *   256 OUT (full)  eq. crit:out: to w in U it costs c(u,w) + min over out-edges
  *                   (w,w') with w' not in S
+ *   512 APPROX(k)   the approximate IN (full) and OUT-WEAK minima of the paper's
+ *                   closing remark in Section 3, in a deterministic schedule: in
+ *                   every k-th phase (phases 1, k+1, 2k+1, ...) each fringe
+ *                   vertex gets the exact IN (full) and OUT-WEAK terms; a vertex
+ *                   that enters F starts from its static minima; when w enters F
+ *                   every fringe v with an edge (w,v) lowers its IN value to
+ *                   c(w,v) if smaller, every fringe u with an edge (u,w) lowers
+ *                   its OUT value to c(u,w) if smaller; nothing else changes the
+ *                   values between recomputations.  A value is then never above
+ *                   the exact term (deletions are ignored: too small is
+ *                   conservative) and never below the static minimum, so the
+ *                   criterion is sound and complete.  k sits in mask bits 10..15
+ *                   (0 means 1).
  * All arithmetic is exact unsigned integer.  "d[v] - x <= minD" is evaluated as
  * d[v] <= minD + x so nothing underflows; an empty minimum is infinite and
  * makes the IN test true and contributes nothing to an OUT threshold.
@@ -51,7 +64,8 @@
 
 enum {
     ORC_IN_STATIC = 1u, ORC_OUT_STATIC = 2u, ORC_IN_SIMPLE = 4u, ORC_OUT_SIMPLE = 8u,
-    ORC_IN_FULL = 16u, ORC_OUT_WEAK = 32u, ORC_DIJK = 64u, ORC_ORACLE = 128u, ORC_OUT_FULL = 256u
+    ORC_IN_FULL = 16u, ORC_OUT_WEAK = 32u, ORC_DIJK = 64u, ORC_ORACLE = 128u, ORC_OUT_FULL = 256u,
+    ORC_APPROX = 512u, ORC_APPROX_K_SHIFT = 10u, ORC_APPROX_K_MASK = 63u
 };
 enum { ST_U = 0, ST_F = 1, ST_S = 2 };
 
@@ -237,8 +251,12 @@ int orc_simulate(uint32_t n, const uint64_t* row_off, const uint32_t* col, const
     uint32_t* Fn = (uint32_t*)malloc(sizeof(uint32_t) * n);
     uint32_t* Sp = (uint32_t*)malloc(sizeof(uint32_t) * n);
     uint64_t* fill = (uint64_t*)malloc(sizeof(uint64_t) * ((size_t)n + 1));
+    uint64_t* ain = (uint64_t*)malloc(sizeof(uint64_t) * n);   /* APPROX: IN values */
+    uint64_t* aout = (uint64_t*)malloc(sizeof(uint64_t) * n);  /* APPROX: OUT-WEAK values */
+    uint32_t* fresh = (uint32_t*)malloc(sizeof(uint32_t) * n);  /* vertices that entered F this phase */
     int rc = 0;
-    if (!g.rro || !g.rsrc || !g.rw || !g.out_st || !g.in_st || !g.st || !F || !Fn || !Sp || !fill) {
+    if (!g.rro || !g.rsrc || !g.rw || !g.out_st || !g.in_st || !g.st || !F || !Fn || !Sp || !fill ||
+        !ain || !aout || !fresh) {
         rc = -1; goto done;
     }
     /* Preprocessing (Section 5): static minima and the in-edge lists. */
@@ -261,6 +279,8 @@ int orc_simulate(uint32_t n, const uint64_t* row_off, const uint32_t* col, const
     for (uint32_t v = 0; v < n; ++v) { d_out[v] = ORC_INF64; settle_phase[v] = 0; }
     d_out[s] = 0;
     g.st[s] = ST_F;
+    ain[s] = w64(g.in_st[s]);
+    aout[s] = w64(g.out_st[s]);
     uint64_t nF = 1, phases = 0, sumF = 0, settled = 0, relaxed = 0;
     F[0] = s;
 
@@ -289,6 +309,21 @@ int orc_simulate(uint32_t n, const uint64_t* row_off, const uint32_t* col, const
                 if (val < minOut[k]) minOut[k] = val;
             }
         }
+        /* APPROX: exact terms in every k-th phase, then the threshold. */
+        uint64_t minOutA = ORC_INF64;
+        if (crit & ORC_APPROX) {
+            uint32_t kk = (crit >> ORC_APPROX_K_SHIFT) & ORC_APPROX_K_MASK;
+            if (kk == 0) kk = 1;
+            if ((phases - 1) % kk == 0)
+                for (uint64_t i = 0; i < nF; ++i) {
+                    ain[F[i]] = in_min(&g, F[i], ORC_IN_FULL);
+                    aout[F[i]] = out_min(&g, F[i], ORC_OUT_WEAK);
+                }
+            for (uint64_t i = 0; i < nF; ++i) {
+                uint64_t val = sat_add(d_out[F[i]], aout[F[i]]);
+                if (val < minOutA) minOutA = val;
+            }
+        }
         /* Select S': every v in F satisfying one of the criteria. */
         uint64_t nS = 0, nFn = 0, degS = 0;
         for (uint64_t i = 0; i < nF; ++i) {
@@ -299,6 +334,7 @@ int orc_simulate(uint32_t n, const uint64_t* row_off, const uint32_t* col, const
                 if (crit & in_bits[k]) sel = dv <= sat_add(minD, in_min(&g, v, in_bits[k]));
             for (int k = 0; k < 4 && !sel; ++k)
                 if (crit & out_bits[k]) sel = dv <= minOut[k];
+            if (!sel && (crit & ORC_APPROX)) sel = dv <= sat_add(minD, ain[v]) || dv <= minOutA;
             if (!sel && (crit & ORC_DIJK)) sel = (v == argmin);
             if (!sel && (crit & ORC_ORACLE)) sel = (dv == dist_ref[v]);
             if (sel) Sp[nS++] = v; else Fn[nFn++] = v;
@@ -308,6 +344,8 @@ int orc_simulate(uint32_t n, const uint64_t* row_off, const uint32_t* col, const
             uint64_t* r = trace + 6 * (phases - 1);
             uint64_t mo = ORC_INF64;
             for (int k = 3; k >= 0; --k) if (crit & out_bits[k]) { mo = minOut[k]; break; }
+            if (mo == ORC_INF64 && !(crit & (ORC_OUT_STATIC | ORC_OUT_SIMPLE | ORC_OUT_WEAK | ORC_OUT_FULL)))
+                mo = minOutA;  /* APPROX alone: its OUT threshold */
             r[0] = nF; r[1] = nS; r[2] = minD; r[3] = mo; r[4] = 0; r[5] = crit;
         }
         /* Settle: move S' to S (before relaxing), check soundness. */
@@ -322,6 +360,7 @@ int orc_simulate(uint32_t n, const uint64_t* row_off, const uint32_t* col, const
         settled += nS;
         relaxed += degS;
         /* Relax all out-edges of S'; newly reached vertices join F. */
+        uint64_t nFresh = 0;
         for (uint64_t i = 0; i < nS; ++i) {
             uint32_t u = Sp[i];
             for (uint64_t e = row_off[u]; e < row_off[u + 1]; ++e) {
@@ -330,9 +369,24 @@ int orc_simulate(uint32_t n, const uint64_t* row_off, const uint32_t* col, const
                 uint64_t cand = d_out[u] + w[e];
                 if (cand < d_out[t]) {
                     d_out[t] = cand;
-                    if (g.st[t] == ST_U) { g.st[t] = ST_F; Fn[nFn++] = t; }
+                    if (g.st[t] == ST_U) { g.st[t] = ST_F; Fn[nFn++] = t; fresh[nFresh++] = t; }
                 }
             }
+        }
+        /* APPROX bookkeeping for the vertices that entered F (every phase, so
+         * the values are right whatever the next phase's criterion is): static
+         * start values first, then every edge between a new fringe vertex and a
+         * fringe vertex lowers the fringe vertex's value. */
+        for (uint64_t i = 0; i < nFresh; ++i) {
+            ain[fresh[i]] = w64(g.in_st[fresh[i]]);
+            aout[fresh[i]] = w64(g.out_st[fresh[i]]);
+        }
+        for (uint64_t i = 0; i < nFresh; ++i) {
+            uint32_t x = fresh[i];
+            for (uint64_t e = row_off[x]; e < row_off[x + 1]; ++e)
+                if (g.st[col[e]] == ST_F && w[e] < ain[col[e]]) ain[col[e]] = w[e];
+            for (uint64_t e = g.rro[x]; e < g.rro[x + 1]; ++e)
+                if (g.st[g.rsrc[e]] == ST_F && g.rw[e] < aout[g.rsrc[e]]) aout[g.rsrc[e]] = g.rw[e];
         }
         uint32_t* tmp = F; F = Fn; Fn = tmp;
         nF = nFn;
@@ -340,6 +394,6 @@ int orc_simulate(uint32_t n, const uint64_t* row_off, const uint32_t* col, const
     stats[0] = phases; stats[1] = sumF; stats[2] = settled; stats[3] = relaxed;
 done:
     free(g.rro); free(g.rsrc); free(g.rw); free(g.out_st); free(g.in_st); free(g.st);
-    free(F); free(Fn); free(Sp); free(fill);
+    free(F); free(Fn); free(Sp); free(fill); free(ain); free(aout); free(fresh);
     return rc;
 }

@@ -196,13 +196,13 @@ __device__ __forceinline__ SpEnt ldcg_sp(const SpEnt* p) {
 // ---------------------------------------------------------------------------
 // Reductions and appends
 
+// Minimum of a u64 over a full warp with two 32-bit warp reductions: the
+// high words first, then the low words of the lanes that hold that high word.
 __device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    unsigned long long t = __shfl_xor_sync(0xFFFFFFFFu, v, o);
-    v = t < v ? t : v;
-  }
-  return v;
+  const uint32_t hi = (uint32_t)(v >> 32), lo = (uint32_t)v;
+  const uint32_t mh = __reduce_min_sync(0xFFFFFFFFu, hi);
+  const uint32_t ml = __reduce_min_sync(0xFFFFFFFFu, hi == mh ? lo : 0xFFFFFFFFu);
+  return ((unsigned long long)mh << 32) | ml;
 }
 
 // Inclusive prefix sum within a full warp.

@@ -897,6 +897,7 @@ __device__ uint64_t solo_episode(const SolveParams& p, const Mode& md, uint64_t 
     uint32_t wk = 0, wr = 0, we = 0, ws = 0;
 #pragma unroll
     for (int j = 0; j < kIt; ++j) {
+      if (warp * 32 + j * nthr >= nF) break;  // (warp-uniform) the rest of the steps are empty
       const bool rl = ((selm[j] >> lane) & 1u) && rdj[j].y > 0;
       wk += __popc(keepm[j]);
       ws += __popc(selm[j]);

@@ -287,6 +287,45 @@ def pin_trace_accounting(O, seed=19):
         assert all(int(t[i, 5]) == crit for i in range(len(t)))
 
 
+def pin_approx_k1_is_full_weak(O, cases=120, seed=20):
+    """APPROX(1) recomputes the exact IN (full) / OUT-WEAK terms in every
+    phase, so it must settle exactly what IN (full) | OUT-WEAK settles."""
+    rng = np.random.default_rng(seed)
+    for _ in range(cases):
+        g = random_tiny_graph(rng, n_max=30, w_max=int(rng.choice([3, 50, 2**20])))
+        s = int(rng.integers(0, g.n))
+        ref = O.dijkstra(g, s)
+        a = O.simulate(g, s, O.APPROX | (1 << 10), dist_ref=ref)
+        b = O.simulate(g, s, O.IN_FULL | O.OUT_WEAK, dist_ref=ref)
+        assert a.phases == b.phases and (a.settle_phase == b.settle_phase).all()
+
+
+def pin_approx_sound_between(O, cases=80, seed=21):
+    """APPROX(k) is sound (the simulator checks against Dijkstra) and, on the
+    same state, selects at least what the static criteria select and at most
+    what IN (full) | OUT-WEAK selects; its OUT threshold lies between the
+    static one and the exact OUT-WEAK one (every value between the static
+    minimum and the exact term)."""
+    rng = np.random.default_rng(seed)
+    for _ in range(cases):
+        g = random_tiny_graph(rng, n_max=30, w_max=int(rng.choice([3, 50, 2**20])))
+        s = int(rng.integers(0, g.n))
+        ref = O.dijkstra(g, s)
+        for k in (2, 3, 8):
+            crit = O.APPROX | (k << 10)
+            base = O.simulate(g, s, crit, dist_ref=ref)
+            for p in range(1, base.phases):
+                sets, thr = [], []
+                for last in (O.IN_STATIC | O.OUT_STATIC, crit, O.IN_FULL | O.OUT_WEAK):
+                    sched = np.array([crit] * p + [last], np.uint32)
+                    sim = O.simulate(g, s, crit, schedule=sched, dist_ref=ref, trace=True)
+                    sets.append(set(np.nonzero(sim.settle_phase == p + 1)[0].tolist()))
+                    thr.append(int(sim.trace[p, 3]))
+                assert sets[0] <= sets[1] <= sets[2]
+                assert thr[0] <= thr[1] <= thr[2], (p, thr)
+
+
 ALL_PINS = [pin_golden_examples, pin_bellman_ford_fuzz, pin_path_enumeration, pin_unit_grid,
             pin_path_graph, pin_out_star, pin_oracle_hops, pin_distance_invariants,
-            pin_soundness_fuzz, pin_strength_chain, pin_trace_accounting]
+            pin_soundness_fuzz, pin_strength_chain, pin_trace_accounting,
+            pin_approx_k1_is_full_weak, pin_approx_sound_between]

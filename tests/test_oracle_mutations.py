@@ -27,8 +27,13 @@ MUTANTS = {
     "new_vertex_not_queued": ("g.st[t] = ST_F; Fn[nFn++] = t;", "g.st[t] = ST_F;"),
     "sum_f_off_by_one": ("sumF += nF;", "sumF += nF - 1;"),
     "bellman_ford_one_round_short": ("round + 1 < n || round == 0", "round + 2 < n"),
-    "minout_misses_first_entry": ("for (uint64_t i = 0; i < nF; ++i) {\n                uint64_t val",
-                                  "for (uint64_t i = 1; i < nF; ++i) {\n                uint64_t val"),
+    "minout_misses_first_entry": ("for (uint64_t i = 0; i < nF; ++i) {\n                uint64_t val = sat_add(d_out[F[i]], out_min(",
+                                  "for (uint64_t i = 1; i < nF; ++i) {\n                uint64_t val = sat_add(d_out[F[i]], out_min("),
+    "approx_skips_in_update": ("if (g.st[col[e]] == ST_F && w[e] < ain[col[e]]) ain[col[e]] = w[e];",
+                               "if (0) ain[col[e]] = w[e];"),
+    "approx_never_recomputes": ("if ((phases - 1) % kk == 0)", "if (phases == 0)"),
+    "approx_out_update_wrong_side": ("if (g.st[g.rsrc[e]] == ST_F && g.rw[e] < aout[g.rsrc[e]]) aout[g.rsrc[e]] = g.rw[e];",
+                                     "if (0) aout[g.rsrc[e]] = g.rw[e];"),
 }
 
 
