@@ -63,9 +63,19 @@ typedef enum {
  *                    unsettled, of c(u,w) for w in F and c(u,w) +
  *                    min_{(w,x) in E} c(w,x) for w unexplored) (eq. crit:outweak)
  *   SSSP_DIJK        the single fringe vertex of minimum d, lowest id on ties (Section 3)
+ *   SSSP_APPROX      approximate IN (full) and OUT-WEAK minima (the closing
+ *                    remark of Section 3), recomputed exactly in every k-th
+ *                    phase (phases 1, k+1, ...; k from SSSP_APPROX_K(k), 1..63,
+ *                    0 = 1); between recomputations a vertex entering F starts
+ *                    from its static minima and lowers the values of its fringe
+ *                    neighbours to the connecting edge's cost, and nothing else
+ *                    changes them.  Every value lies between the static
+ *                    minimum and the exact term, so the test
+ *                    d[v] <= minD + inA(v) or d[v] <= min_{u in F}(d[u] + outA(u))
+ *                    is sound and complete.
  * An empty minimum is infinite: the IN test then holds, and the vertex adds
- * nothing to the OUT threshold.  IN_SIMPLE and IN_FULL need a graph built
- * with SSSP_GRAPH_REVERSE.  "IN+OUT" = SSSP_IN_STATIC | SSSP_OUT_STATIC is the
+ * nothing to the OUT threshold.  IN_SIMPLE, IN_FULL and APPROX need a graph
+ * built with SSSP_GRAPH_REVERSE.  "IN+OUT" = SSSP_IN_STATIC | SSSP_OUT_STATIC is the
  * criterion of the paper's implementation (Section 5). */
 enum {
   SSSP_IN_STATIC = 1u << 0,
@@ -75,6 +85,8 @@ enum {
   SSSP_IN_FULL = 1u << 4,
   SSSP_OUT_WEAK = 1u << 5,
   SSSP_DIJK = 1u << 6,
+  SSSP_APPROX = 1u << 9,
+  SSSP_APPROX_K_SHIFT = 10, /* bits 10..15: k of SSSP_APPROX */
   SSSP_CRITERIA_MASK = 0xFFFFu,
   /* Execution options (do not change results, only speed). */
   SSSP_POLICY_LEARNED = 1u << 16,  /* per-phase arm chosen by the loaded policy network (below) */
@@ -234,6 +246,7 @@ sssp_status sssp_batch_autotune(sssp_batch* b, void* stream, uint32_t* bpg_out, 
  *   log2(n)/32, (m/n)/32, S'/(1+F')
  * with E', S', F' the relaxed edges, settled vertices and fringe size of the
  * previous phase and k the phase index. */
+#define SSSP_APPROX_K(k) (SSSP_APPROX | (((uint32_t)(k) & 63u) << SSSP_APPROX_K_SHIFT))
 #define SSSP_POLICY_FEATURES 8
 #define SSSP_POLICY_ARMS 4
 #define SSSP_POLICY_WEIGHTS 1476

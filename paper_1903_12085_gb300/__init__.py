@@ -30,6 +30,15 @@ OUT_SIMPLE = 1 << 3
 IN_FULL = 1 << 4
 OUT_WEAK = 1 << 5
 DIJK = 1 << 6
+APPROX = 1 << 9
+
+
+def approx(k: int) -> int:
+    """SSSP_APPROX_K(k): approximate IN (full) / OUT-WEAK minima recomputed in
+    every k-th phase (1 <= k <= 63)."""
+    if not 1 <= k <= 63:
+        raise ValueError("k must be in 1..63")
+    return APPROX | (k << 10)
 POLICY_LEARNED = 1 << 16
 FRONTIER_DENSE = 1 << 17
 FRONTIER_AUTO = 1 << 18

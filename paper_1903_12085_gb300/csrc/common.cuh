@@ -93,6 +93,9 @@ struct PhaseSlot {
   unsigned int fsize;             // |F| at the start of the phase (queue + far part)
   unsigned int pad;
   unsigned long long t_select;    // %globaltimer when the selection step ended (trace)
+  unsigned long long a_min_apx;   // APPROX's OUT threshold of this phase
+  unsigned int fresh_count;       // vertices that entered F in the relax step before this phase
+  unsigned int pad2;
 };
 
 // Per-solve control block in device memory (zeroed before each launch).
@@ -124,6 +127,9 @@ struct SolveWS {
   uint32_t* im_dyn;        // [n] dynamic in-minimum of fringe vertices (IN-SIMPLE phases), or nullptr
   uint32_t* tile_owner;    // [m / tile + 2] relax-list entry holding each tile's first edge, or nullptr
   unsigned long long* im_full;  // [n] IN (full) minima of fringe vertices (IN_FULL phases), or nullptr
+  unsigned long long* apx_in;   // [n] APPROX: approximate IN (full) values, or nullptr
+  unsigned long long* apx_out;  // [n] APPROX: approximate OUT-WEAK values
+  uint32_t* fresh;              // [n] APPROX: vertices that entered F in the last relax step
   unsigned long long* dist;  // [n] output distances
   Ctl* ctl;
   uint32_t* settle_phase;  // [n] optional

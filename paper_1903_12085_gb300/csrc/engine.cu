@@ -198,6 +198,8 @@ struct Mode {
   bool out_dyn;      // OUT-SIMPLE (three-step kind)
   bool out_weak;     // OUT-WEAK (three-step kind)
   bool in_full;      // IN (full) (three-step kind)
+  bool approx;       // APPROX(k) (three-step kind)
+  uint32_t apx_k;    // its recomputation interval
   bool dijk;
   bool nearfar;      // the fringe may be split into a near queue and a far part
 };
@@ -213,7 +215,10 @@ __device__ __forceinline__ Mode mode_of(const SolveParams& p) {
   m.out_dyn = (crit & SSSP_OUT_SIMPLE) != 0;
   m.use_out = m.out_dyn || m.out_weak || (crit & SSSP_OUT_STATIC) != 0;
   m.dijk = (crit & SSSP_DIJK) != 0;
-  m.fused = !m.out_dyn && !m.out_weak && !m.in_full && !m.dijk;
+  m.approx = (crit & SSSP_APPROX) != 0 && p.ws.apx_in != nullptr;
+  m.apx_k = (crit >> SSSP_APPROX_K_SHIFT) & 63u;
+  if (m.apx_k == 0) m.apx_k = 1;
+  m.fused = !m.out_dyn && !m.out_weak && !m.in_full && !m.dijk && !m.approx;
   const bool policy = (crit & SSSP_POLICY_LEARNED) != 0;
   m.use_in = (crit & (SSSP_IN_STATIC | SSSP_IN_SIMPLE | SSSP_IN_FULL)) != 0 || policy;
   m.nearfar = m.fused && !(crit & SSSP_IN_SIMPLE) && p.nf_min != 0 && p.g.n <= kNearFarMaxVertices;
@@ -292,6 +297,8 @@ __device__ __forceinline__ void reset_slot(PhaseSlot* s) {
   s->settled_now = 0;
   s->arm = 0;
   s->fsize = 0;
+  s->a_min_apx = kInf64;
+  s->fresh_count = 0;
 }
 
 // Relaxation of one edge (u -> t) with d[u] = du (step C, any mode): one
@@ -387,7 +394,7 @@ __device__ bool phase_select(const SolveParams& p, const Grp& grp, const Mode& m
   }
 
   // ---- thresholds
-  unsigned long long minD, minOut;
+  unsigned long long minD, minOut, min_apx = kInf64;
   if (md.fused) {
     minD = ldcg_u64(&S0->min_d);
     minOut = ldcg_u64(&S0->min_out);
@@ -407,8 +414,34 @@ __device__ bool phase_select(const SolveParams& p, const Grp& grp, const Mode& m
       if (!grp.sync()) return false;
     }
   } else {
+    const bool apx_recompute = md.approx && (k - 1) % md.apx_k == 0;
+    if (md.approx && !apx_recompute) {
+      // APPROX bookkeeping for the vertices that entered F in the last relax
+      // step: static start values, then every edge between such a vertex and
+      // a fringe vertex lowers the fringe vertex's value to the edge's cost
+      const uint32_t nfr = ldcg_u32(&S0->fresh_count);
+      for (uint64_t i = gtid; i < nfr; i += gthreads) {
+        const uint32_t x = ldcg_u32(&w.fresh[i]);
+        const uint32_t im = __ldg(&g.in_min[x]), om = __ldg(&g.out_min[x]);
+        w.apx_in[x] = im == kInf32 ? kInf64 : im;
+        w.apx_out[x] = om == kInf32 ? kInf64 : om;
+      }
+      if (!grp.sync()) return false;
+      for (uint64_t i = gtid; i < nfr; i += gthreads) {
+        const uint32_t x = ldcg_u32(&w.fresh[i]);
+        for (uint64_t e = __ldg(&g.row_off[x]), e1 = __ldg(&g.row_off[x + 1]); e < e1; ++e) {
+          const uint2 ed = __ldg(&g.edges[e]);
+          if (ldcg_u8(&w.status[ed.x]) == kF) atomicMin(&w.apx_in[ed.x], (unsigned long long)ed.y);
+        }
+        for (uint64_t e = __ldg(&g.rrow_off[x]), e1 = __ldg(&g.rrow_off[x + 1]); e < e1; ++e) {
+          const uint2 ed = __ldg(&g.redges[e]);
+          if (ldcg_u8(&w.status[ed.x]) == kF) atomicMin(&w.apx_out[ed.x], (unsigned long long)ed.y);
+        }
+      }
+      if (!grp.sync()) return false;
+    }
     // A: thresholds over the phase-start state, advancing cursors lazily
-    unsigned long long lmin_d = kInf64, lmin_out = kInf64;
+    unsigned long long lmin_d = kInf64, lmin_out = kInf64, lmin_apx = kInf64;
     auto visit = [&](uint32_t v) {
       const unsigned long long dv = ldcg_u64(&w.vrec[v].d);
       lmin_d = dv < lmin_d ? dv : lmin_d;
@@ -427,6 +460,20 @@ __device__ bool phase_select(const SolveParams& p, const Grp& grp, const Mode& m
       }
       if (md.in_full) w.im_full[v] = in_min_full(g, w, v);
       else if (in_dyn) w.im_dyn[v] = in_min_dynamic(g, w, v, false);
+      if (md.approx) {  // exact terms in every k-th phase, then APPROX's OUT threshold
+        unsigned long long ao;
+        if (apx_recompute) {
+          w.apx_in[v] = in_min_full(g, w, v);
+          ao = out_min_weak(g, w, v);
+          w.apx_out[v] = ao;
+        } else {
+          ao = ldcg_u64(&w.apx_out[v]);
+        }
+        if (ao != kInf64) {
+          const unsigned long long x = dv + ao;
+          lmin_apx = x < lmin_apx ? x : lmin_apx;
+        }
+      }
     };
     if (dense) {
       for (uint64_t v = gtid; v < n; v += gthreads)
@@ -435,9 +482,11 @@ __device__ bool phase_select(const SolveParams& p, const Grp& grp, const Mode& m
       for (uint64_t i = gtid; i < nF; i += gthreads) visit(ldcg_u32(&Q[i]));
     }
     block_min2_to_global(lmin_d, lmin_out, &S0->a_min_d, md.use_out ? &S0->a_min_out : nullptr, sh.red);
+    if (md.approx) block_min2_to_global(lmin_apx, kInf64, &S0->a_min_apx, nullptr, sh.red);
     if (!grp.sync()) return false;
     minD = ldcg_u64(&S0->a_min_d);
     minOut = ldcg_u64(&S0->a_min_out);
+    if (md.approx) min_apx = ldcg_u64(&S0->a_min_apx);
   }
   uint32_t amin = kInf32;
   if (md.dijk) {  // DIJK: the lowest id among fringe vertices of minimum d
@@ -508,6 +557,10 @@ __device__ bool phase_select(const SolveParams& p, const Grp& grp, const Mode& m
         }
       }
       if (!sel && md.use_out) sel = dv <= minOut;
+      if (!sel && md.approx) {
+        const unsigned long long ai = ldcg_u64(&w.apx_in[v]);
+        sel = ai == kInf64 || dv <= minD + ai || dv <= min_apx;
+      }
       if (!sel && md.dijk) sel = (v == amin);
       if (sel) {
         w.status[v] = kS;
@@ -643,18 +696,28 @@ __device__ bool phase_relax(const SolveParams& p, const Grp& grp, const Mode& md
         }
       }
     }
-    // vertices new to F: one block scan and one atomic per tile
+    // vertices new to F: one block scan and one atomic per tile (APPROX also
+    // lists them for the next phase's bookkeeping)
     uint32_t tf;
     const uint32_t pf = block_exclusive_scan(__popc(fmask), sh.scan, &tf);
-    if (tid == 0) sh.bases[0] = tf ? atomicAdd(&S1->qcount, tf) : 0u;
+    if (tid == 0) {
+      sh.bases[0] = tf ? atomicAdd(&S1->qcount, tf) : 0u;
+      if (md.approx) sh.bases[1] = tf ? atomicAdd(&S1->fresh_count, tf) : 0u;
+    }
     __syncthreads();
     uint32_t fslot = (uint32_t)sh.bases[0] + pf;
+    uint32_t xslot = md.approx ? (uint32_t)sh.bases[1] + pf : 0u;
 #pragma unroll
     for (int it = 0; it < kRelaxItems; ++it)
       if ((fmask >> it) & 1u) {
         if (fslot < n) Qn[fslot] = fv[it];
         else atomicCAS(&ctl->err, 0, (int)SSSP_ERR_INTERNAL);
         ++fslot;
+        if (md.approx) {
+          if (xslot < n) w.fresh[xslot] = fv[it];
+          else atomicCAS(&ctl->err, 0, (int)SSSP_ERR_INTERNAL);
+          ++xslot;
+        }
       }
     __syncthreads();
   }
@@ -678,7 +741,8 @@ __device__ bool phase_relax(const SolveParams& p, const Grp& grp, const Mode& md
       r.frontier = ldcg_u32(&S0->fsize);
       r.settled = settled_now;
       r.min_d = md.fused ? ldcg_u64(&S0->min_d) : ldcg_u64(&S0->a_min_d);
-      r.min_out = md.use_out ? (md.fused ? ldcg_u64(&S0->min_out) : ldcg_u64(&S0->a_min_out)) : kInf64;
+      r.min_out = md.use_out ? (md.fused ? ldcg_u64(&S0->min_out) : ldcg_u64(&S0->a_min_out))
+                             : (md.approx ? ldcg_u64(&S0->a_min_apx) : kInf64);
       r.deg_settled = E;
       uint32_t c = p.crit & SSSP_CRITERIA_MASK;
       if (md.use_in) c = (c & ~(uint32_t)(SSSP_IN_STATIC | SSSP_IN_SIMPLE)) | (in_dyn ? SSSP_IN_SIMPLE : SSSP_IN_STATIC);
@@ -1639,7 +1703,8 @@ sssp_status ensure_kernel_attrs() {
 
 sssp_status check_crit(const sssp_graph* g, uint32_t crit) {
   const uint32_t known = SSSP_IN_STATIC | SSSP_OUT_STATIC | SSSP_IN_SIMPLE | SSSP_OUT_SIMPLE | SSSP_IN_FULL |
-                         SSSP_OUT_WEAK | SSSP_DIJK | SSSP_FRONTIER_DENSE | SSSP_FRONTIER_AUTO | SSSP_POLICY_LEARNED;
+                         SSSP_OUT_WEAK | SSSP_DIJK | SSSP_APPROX | (63u << SSSP_APPROX_K_SHIFT) |
+                         SSSP_FRONTIER_DENSE | SSSP_FRONTIER_AUTO | SSSP_POLICY_LEARNED;
   if ((crit & SSSP_CRITERIA_MASK) == 0) return fail(SSSP_ERR_INVALID_ARG, "criterion mask has no criterion bit");
   if (crit & ~known) return fail(SSSP_ERR_INVALID_ARG, "unknown criterion bits 0x%x", crit & ~known);
   if (crit & SSSP_POLICY_LEARNED) {
@@ -1647,8 +1712,10 @@ sssp_status check_crit(const sssp_graph* g, uint32_t crit) {
     if ((crit & SSSP_CRITERIA_MASK) != (SSSP_IN_STATIC | SSSP_OUT_STATIC))
       return fail(SSSP_ERR_INVALID_ARG, "SSSP_POLICY_LEARNED takes IN_STATIC | OUT_STATIC as its fallback arm");
   }
-  if ((crit & (SSSP_IN_SIMPLE | SSSP_IN_FULL)) && !g->rrow_off)
-    return fail(SSSP_ERR_UNSUPPORTED, "IN-SIMPLE and IN (full) need a graph built with SSSP_GRAPH_REVERSE");
+  if ((crit & (63u << SSSP_APPROX_K_SHIFT)) && !(crit & SSSP_APPROX))
+    return fail(SSSP_ERR_INVALID_ARG, "criterion bits 10..15 (k) are set without SSSP_APPROX");
+  if ((crit & (SSSP_IN_SIMPLE | SSSP_IN_FULL | SSSP_APPROX)) && !g->rrow_off)
+    return fail(SSSP_ERR_UNSUPPORTED, "IN-SIMPLE, IN (full) and APPROX need a graph built with SSSP_GRAPH_REVERSE");
   return SSSP_OK;
 }
 
@@ -1680,6 +1747,9 @@ void workspace_free(Workspace* ws) {
   cudaFree(ws->im_dyn);
   cudaFree(ws->tile_owner);
   cudaFree(ws->im_full);
+  cudaFree(ws->apx_in);
+  cudaFree(ws->apx_out);
+  cudaFree(ws->fresh);
   cudaFree(ws->dist);
   cudaFree(ws->ctl);
   cudaFreeHost(ws->ctl_host);
@@ -1698,7 +1768,9 @@ sssp_status workspace_alloc(uint32_t n, uint64_t m, bool want_cursors, bool want
     return s;
   }
   if (want_cursors && ((s = dev_alloc(&ws->cur_out, n)) || (s = dev_alloc(&ws->cur_in, n)) ||
-                       (s = dev_alloc(&ws->im_dyn, n)) || (s = dev_alloc(&ws->im_full, n)))) {
+                       (s = dev_alloc(&ws->im_dyn, n)) || (s = dev_alloc(&ws->im_full, n)) ||
+                       (s = dev_alloc(&ws->apx_in, n)) || (s = dev_alloc(&ws->apx_out, n)) ||
+                       (s = dev_alloc(&ws->fresh, n)))) {
     workspace_free(ws);
     return s;
   }
@@ -1739,6 +1811,10 @@ SolveWS ws_view(Workspace* ws, unsigned long long* dist, uint32_t crit, bool has
   w.im_dyn = w.cur_in ? ws->im_dyn : nullptr;
   w.tile_owner = ws->tile_owner;
   w.im_full = ((crit & SSSP_IN_FULL) && has_reverse) ? ws->im_full : nullptr;
+  const bool apx = (crit & SSSP_APPROX) && has_reverse;
+  w.apx_in = apx ? ws->apx_in : nullptr;
+  w.apx_out = apx ? ws->apx_out : nullptr;
+  w.fresh = apx ? ws->fresh : nullptr;
   w.ctl = ws->ctl;
   return w;
 }
@@ -1903,7 +1979,7 @@ sssp_status batch_build(sssp_graph* const* graphs, const uint32_t* sources, uint
   });
   std::vector<BatchItem> h(count);
   b->ws.assign(count, nullptr);
-  const bool cursors = (crit & (SSSP_IN_SIMPLE | SSSP_OUT_SIMPLE | SSSP_IN_FULL)) != 0;
+  const bool cursors = (crit & (SSSP_IN_SIMPLE | SSSP_OUT_SIMPLE | SSSP_IN_FULL | SSSP_APPROX)) != 0;
   for (uint32_t k = 0; k < count; ++k) {
     const uint32_t i = order[k];
     if ((s = workspace_alloc(graphs[i]->n, graphs[i]->m, cursors, false, &b->ws[k])) != SSSP_OK) {

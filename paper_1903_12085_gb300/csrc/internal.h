@@ -84,6 +84,9 @@ struct Workspace {
   uint32_t* im_dyn;
   uint32_t* tile_owner;      // [m / kTile + 2] relax-list entry holding the first edge of each tile
   unsigned long long* im_full;  // [n] IN (full) minima (allocated with the cursors)
+  unsigned long long* apx_in;   // [n] APPROX values (allocated with the cursors)
+  unsigned long long* apx_out;  // [n]
+  uint32_t* fresh;              // [n]
   unsigned long long* dist;  // used when the caller's distance buffer is host memory
   Ctl* ctl;
   Ctl* ctl_host;  // pinned mirror for read-back

@@ -17,7 +17,8 @@ pytestmark = pytest.mark.gpu
 
 CRITS = [sp.IN_STATIC, sp.OUT_STATIC, sp.IN_OUT, sp.IN_SIMPLE, sp.OUT_SIMPLE, sp.SIMPLE,
          sp.IN_STATIC | sp.OUT_SIMPLE, sp.IN_SIMPLE | sp.OUT_STATIC,
-         sp.IN_FULL, sp.OUT_WEAK, sp.IN_FULL | sp.OUT_WEAK, sp.IN_FULL | sp.OUT_STATIC]
+         sp.IN_FULL, sp.OUT_WEAK, sp.IN_FULL | sp.OUT_WEAK, sp.IN_FULL | sp.OUT_STATIC,
+         sp.approx(1), sp.approx(3), sp.approx(8) | sp.DIJK]
 MODES = [0, sp.FRONTIER_DENSE, sp.FRONTIER_AUTO]
 
 
@@ -122,7 +123,7 @@ def test_workload_shapes_small(tuning):
         G = sp.Graph.from_csr(g, reverse=True)
         for _, s in wl.solves[:2]:
             ref = oracle.dijkstra(g, s)
-            for crit in [sp.IN_OUT, sp.SIMPLE, sp.IN_FULL | sp.OUT_WEAK]:
+            for crit in [sp.IN_OUT, sp.SIMPLE, sp.IN_FULL | sp.OUT_WEAK, sp.approx(4)]:
                 for mode in MODES:
                     check(g, G, s, crit, ref, mode)
 
