@@ -238,7 +238,8 @@ sssp_status sssp_batch_autotune(sssp_batch* b, void* stream, uint32_t* bpg_out, 
  * Network: W1[8][32] b1[32] W2[32][32] b2[32] W3[32][4] b3[4] (float32,
  * input index first, ReLU after both hidden layers); outputs are predicted
  * log2(phase time / settled vertices) per arm; the smallest one wins if it
- * is below arm 0's by a margin of 0.35, else arm 0 runs.  While the fringe is
+ * is below arm 0's by a margin of 0.35, else arm 0 runs; the dense arms take
+ * part only while |F| >= n/32.  While the fringe is
  * split into near and far parts (sssp_tuning's nearfar fields) every phase
  * runs arm 0, whose sparse queue is then the near part.
  * Features (sssp_policy_features computes them on the host):

@@ -270,7 +270,7 @@ __device__ Arm choose_arm(const SolveParams& p, uint64_t k, uint32_t nQ, uint32_
     float f[kPolFeat], y[kPolArms];
     policy_features(f, nF, p.g.n, p.g.m, k, e_prev, s_prev, f_prev);
     policy_forward_warp(policy_smem(), f, y);
-    if (threadIdx.x == 0) s_arm = policy_pick(y, p.ws.cur_in != nullptr);
+    if (threadIdx.x == 0) s_arm = policy_pick(y, p.ws.cur_in != nullptr, (uint64_t)nF * 32 >= p.g.n);
   }
   __syncthreads();
   Arm a;

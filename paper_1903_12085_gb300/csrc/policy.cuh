@@ -85,11 +85,15 @@ __device__ __forceinline__ void policy_forward_warp(const float* __restrict__ w,
 // saves; arm 0 if any allowed prediction is not finite.
 constexpr float kPolicyMargin = 0.35f;
 
-__device__ __forceinline__ int policy_pick(const float* y, bool allow_simple) {
+// allow_dense = false (a fringe below n/32) leaves out the dense arms: a scan of
+// all n vertices then costs far more per settled vertex than on the small
+// training graphs the network has seen.
+__device__ __forceinline__ int policy_pick(const float* y, bool allow_simple, bool allow_dense) {
   const int na = allow_simple ? 4 : 2;
   int best = 0;
   for (int a = 0; a < na; ++a) {
     if (!isfinite(y[a])) return 0;
+    if ((a & 1) && !allow_dense) continue;
     if (y[a] < y[best]) best = a;
   }
   return y[best] < y[0] - kPolicyMargin ? best : 0;

@@ -34,7 +34,7 @@ def phase_samples(trace, n: int, m: int, arm: int):
     return X, T, A
 
 
-def collect(cases, arms=None, repeats: int = 2):
+def collect(cases, arms=None, repeats: int = 3):
     """cases: list of (Graph built with reverse=True, source).  Runs every arm
     `repeats` times (the first run of each warms up) and returns X [N,8]
     float32, T [N] float32, A [N] uint32."""
