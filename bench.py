@@ -61,7 +61,7 @@ def parse():
 # workload name and criterion, with a hash of the engine sources the capture ran
 # on: once the kernel changes the figure no longer applies and is reported null.
 MEASURED_TRAFFIC = {
-    ("grid_1024x1024", "in_out"): (52034560 + 8113664, "9244790d4936733f"),
+    ("grid_1024x1024", "in_out"): (51623168 + 7831296, "5d15d214d58e8e2b"),
 }
 ENGINE_SOURCES = ("engine.cu", "engine.h", "common.cuh", "policy.cuh")
 
