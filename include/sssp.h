@@ -214,12 +214,15 @@ sssp_status sssp_batch_create(sssp_graph* const* graphs, const uint32_t* sources
 sssp_status sssp_batch_launch(sssp_batch* b, void* stream);
 void sssp_batch_destroy(sssp_batch* b);
 
-/* Autotuner of a prepared batch: runs the batch with every candidate number
- * of blocks per solve (the batch's own choice, 1, 2, 4, ... and all
- * co-resident blocks), each once to warm up and three times timed with CUDA
- * events on `stream`, keeps the candidate with the smallest median (another
- * candidate must beat the batch's own choice by 3 %) and re-captures the CUDA
- * graph with it.  Results never depend on the choice (the
+/* Autotuner of a prepared batch: picks the number of blocks per solve from
+ * the ladder 1, 2, 4, ..., all co-resident blocks (plus the batch's own
+ * choice).  It times the batch's own choice, then walks up and then down the
+ * ladder from it; every candidate runs once to warm up and three times timed
+ * with CUDA events on `stream` (scored by the median), and a walk stops at the
+ * first candidate more than 10 % slower than the best so far, or whose warm-up
+ * alone took 1.5 times the best median (it gets no timed runs).  Another
+ * candidate must beat the batch's own choice by 3 %.  The CUDA graph is
+ * re-captured with the winner.  Results never depend on the choice (the
  * outputs hold the last run's, identical to any other run's).  bpg_out and
  * ms_out (either may be NULL) get the chosen value and its launch time.
  * Synchronous.  A library feature with no counterpart in the paper. */

@@ -2125,40 +2125,70 @@ extern "C" sssp_status sssp_batch_autotune(sssp_batch* b, void* stream, uint32_t
   if (!b) return fail(SSSP_ERR_INVALID_ARG, "batch is NULL");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const uint32_t resident = (uint32_t)(g_blocks_per_sm * sm_count());
-  // candidates: the batch's own choice (first), powers of two and the full
-  // grid; each runs once to warm up and kTimed times, scored by the median
+  // candidates: 1, 2, 4, ..., all co-resident blocks, and the batch's own
+  // choice.  The search starts at the batch's choice and walks up and then
+  // down the ladder; a walk stops at the first candidate that is clearly
+  // slower than the best so far (launch time is unimodal in practice, and a
+  // launch with many blocks per solve can run for seconds on deep solves).
+  // Each candidate's warm-up launch is timed too: one already kWarmCut times
+  // the best median gets no timed runs.  Timed runs: kTimed, scored by the
+  // median.
   constexpr int kTimed = 3;
+  constexpr float kWarmCut = 1.5f, kStopCut = 1.1f, kKeepOwn = 0.97f;
   const uint32_t bpg0 = b->bpg;
-  std::vector<uint32_t> cand{bpg0};
-  for (uint32_t c = 1; c < resident; c *= 2)
-    if (c != bpg0) cand.push_back(c);
-  if (resident != bpg0) cand.push_back(resident);
-  cudaEvent_t ev[kTimed + 1];
+  std::vector<uint32_t> ladder;
+  for (uint32_t c = 1; c < resident; c *= 2) ladder.push_back(c);
+  ladder.push_back(resident);
+  if (std::find(ladder.begin(), ladder.end(), bpg0) == ladder.end()) ladder.push_back(bpg0);
+  std::sort(ladder.begin(), ladder.end());
+  const int i0 = (int)(std::find(ladder.begin(), ladder.end(), bpg0) - ladder.begin());
+  cudaEvent_t ev[kTimed + 2];
   for (auto& e : ev) SSSP_CUDA_TRY(cudaEventCreate(&e));
   uint32_t best = bpg0;
   float best_ms = -1.0f, first_ms = -1.0f;
   sssp_status s = SSSP_OK;
-  for (uint32_t c : cand) {
+  // times candidate c; returns its median launch time, or a negative value if
+  // the warm-up alone was kWarmCut times the best median
+  auto measure = [&](uint32_t c, float* out) -> sssp_status {
     b->bpg = c;
     b->groups = std::max<uint32_t>(1, std::min<uint32_t>(b->count, resident / c));
-    if ((s = batch_enqueue(b, st)) != SSSP_OK) break;  // warm-up
-    if (cudaEventRecord(ev[0], st) != cudaSuccess) s = fail(SSSP_ERR_CUDA, "timing a batch launch failed");
-    for (int r = 0; r < kTimed && s == SSSP_OK; ++r) {
-      if ((s = batch_enqueue(b, st)) == SSSP_OK && cudaEventRecord(ev[r + 1], st) != cudaSuccess)
-        s = fail(SSSP_ERR_CUDA, "timing a batch launch failed");
+    sssp_status r = SSSP_OK;
+    if (cudaEventRecord(ev[0], st) != cudaSuccess) return fail(SSSP_ERR_CUDA, "timing a batch launch failed");
+    if ((r = batch_enqueue(b, st)) != SSSP_OK) return r;  // warm-up
+    if (cudaEventRecord(ev[1], st) != cudaSuccess || cudaEventSynchronize(ev[1]) != cudaSuccess)
+      return fail(SSSP_ERR_CUDA, "timing a batch launch failed");
+    if ((r = batch_status(b)) != SSSP_OK) return r;
+    float warm = 0.0f;
+    cudaEventElapsedTime(&warm, ev[0], ev[1]);
+    if (best_ms > 0.0f && warm > kWarmCut * best_ms) {
+      *out = -1.0f;
+      return SSSP_OK;
     }
-    if (s == SSSP_OK && cudaEventSynchronize(ev[kTimed]) != cudaSuccess)
-      s = fail(SSSP_ERR_CUDA, "timing a batch launch failed");
-    if (s != SSSP_OK || (s = batch_status(b)) != SSSP_OK) break;
+    for (int i = 0; i < kTimed; ++i) {
+      if ((r = batch_enqueue(b, st)) != SSSP_OK) return r;
+      if (cudaEventRecord(ev[i + 2], st) != cudaSuccess) return fail(SSSP_ERR_CUDA, "timing a batch launch failed");
+    }
+    if (cudaEventSynchronize(ev[kTimed + 1]) != cudaSuccess) return fail(SSSP_ERR_CUDA, "timing a batch launch failed");
+    if ((r = batch_status(b)) != SSSP_OK) return r;
     float t[kTimed];
-    for (int r = 0; r < kTimed; ++r) cudaEventElapsedTime(&t[r], ev[r], ev[r + 1]);
+    for (int i = 0; i < kTimed; ++i) cudaEventElapsedTime(&t[i], ev[i + 1], ev[i + 2]);
     std::sort(t, t + kTimed);
-    const float ms = t[kTimed / 2];
-    if (first_ms < 0.0f) first_ms = ms;
-    // another candidate replaces the batch's own choice only if clearly faster
-    if (best_ms < 0.0f || (ms < best_ms && ms < 0.97f * first_ms)) {
-      best_ms = ms;
-      best = c;
+    *out = t[kTimed / 2];
+    return SSSP_OK;
+  };
+  float ms = 0.0f;
+  if ((s = measure(bpg0, &ms)) == SSSP_OK) {
+    best_ms = first_ms = ms;
+    for (int dir : {+1, -1}) {
+      for (int i = i0 + dir; s == SSSP_OK && i >= 0 && i < (int)ladder.size(); i += dir) {
+        if ((s = measure(ladder[i], &ms)) != SSSP_OK || ms < 0.0f) break;
+        // another candidate replaces the batch's own choice only if clearly faster
+        if (ms < best_ms && ms < kKeepOwn * first_ms) {
+          best_ms = ms;
+          best = ladder[i];
+        }
+        if (ms > kStopCut * best_ms) break;
+      }
     }
   }
   for (auto& e : ev) cudaEventDestroy(e);

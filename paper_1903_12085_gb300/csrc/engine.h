@@ -6,8 +6,8 @@
 namespace sssp {
 
 constexpr int kThreads = 512;
-constexpr int kRelaxItems = 4;
-constexpr int kSelItems = 4;  // fringe entries per thread per selection chunk
+constexpr int kRelaxItems = 2;
+constexpr int kSelItems = 2;  // fringe entries per thread per selection chunk
 constexpr int kTile = kThreads * kRelaxItems;
 // Solo mode (one block runs whole phases with its queues in shared memory):
 // fringe and relax list hold at most kSoloCap entries.

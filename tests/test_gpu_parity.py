@@ -319,8 +319,9 @@ def test_prepared_batch_replays():
 
 
 def test_batch_autotune_keeps_results():
-    """The autotuner times every blocks-per-solve candidate and re-captures the
-    launch with the fastest; the replayed batch still gives the oracle's output."""
+    """The autotuner walks the blocks-per-solve ladder and re-captures the launch
+    with the fastest candidate it timed; the replayed batch still gives the
+    oracle's output."""
     wl = gg.workload(4, shrink=5)
     Gs = [sp.Graph.from_csr(g) for g in wl.graphs]
     B = sp.Batch([Gs[i] for i, _ in wl.solves], [s for _, s in wl.solves], sp.IN_OUT)
