@@ -95,11 +95,13 @@ def train(X, T, A, epochs: int = 2000, lr: float = 1e-2, seed: int = 0, log_ever
 
 def training_cases(shrink_base: int = 0):
     """Seeded training graphs of every family, none of them a benchmark or
-    held-out test graph: uniform G(n,m) from 2^13 to 2^22 vertices, R-MAT from
+    held-out test graph: uniform G(n,m) from 2^13 to 2^22 vertices (the
+    2^14-vertex one drawn with its own seed, not the benchmark's), R-MAT from
     scale 12 to 20 and grids (sources from their own recipes)."""
     import graphgen as gg
 
-    wls = [gg.workload(1), gg.workload(1, shrink=1), gg.workload(3, shrink=2 + shrink_base),
+    g14 = gg.gnm(16384, 131072, 0, 1 << 24, gg.SEED_BASE + 201)
+    wls = [gg.Workload(g14.name, [g14], [(0, 0)]), gg.workload(1, shrink=1), gg.workload(3, shrink=2 + shrink_base),
            gg.workload(5, shrink=2 + shrink_base), gg.workload(3, shrink=8 + shrink_base),
            gg.workload(3, shrink=10 + shrink_base), gg.workload(5, shrink=5 + shrink_base),
            gg.workload(5, shrink=6 + shrink_base),
