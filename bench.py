@@ -62,7 +62,7 @@ def parse():
 # workload name and criterion, with a hash of the engine sources the capture ran
 # on: once the kernel changes the figure no longer applies and is reported null.
 MEASURED_TRAFFIC = {
-    ("grid_1024x1024", "in_out"): (51623168 + 7831296, "5d15d214d58e8e2b"),
+    ("grid_1024x1024", "in_out"): (52220672 + 7912192, "9afd8ba9ec29eacd"),
 }
 ENGINE_SOURCES = ("engine.cu", "engine.h", "common.cuh", "policy.cuh")
 
