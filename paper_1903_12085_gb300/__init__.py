@@ -379,8 +379,9 @@ class Batch:
         _check(lib().sssp_batch_launch(self.handle, _stream_ptr(stream)))
 
     def autotune(self, stream=None):
-        """sssp_batch_autotune: time every blocks-per-solve candidate, keep the
-        fastest; returns (blocks per solve, ms per launch)."""
+        """sssp_batch_autotune: walk the blocks-per-solve ladder from the
+        batch's own choice, keep the fastest candidate timed; returns (blocks
+        per solve, ms per launch)."""
         bpg = ctypes.c_uint32()
         ms = ctypes.c_float()
         _check(lib().sssp_batch_autotune(self.handle, _stream_ptr(stream), ctypes.byref(bpg), ctypes.byref(ms)))
