@@ -49,7 +49,8 @@ def parse():
     ap.add_argument("--shrink", type=int, default=0,
                     help="a smaller member of the workload's family (sizes / 2^shrink), for profiling captures")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--criterion", default="in_out", choices=["in_out", "simple", "learned"])
+    ap.add_argument("--criterion", default="in_out", choices=["in_out", "simple", "learned", "full_weak", "approx4"],
+                    help="full_weak = IN (full) | OUT-WEAK; approx4 = approximate minima recomputed every 4th phase")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-policy", action="store_true", help="skip training/timing the learned policy")
     ap.add_argument("--batch-sources", type=int, default=152,
@@ -184,7 +185,8 @@ def build_workload(k: int, shrink: int = 0):
 
 
 def crit_value(sp, name):
-    return {"in_out": sp.IN_OUT, "simple": sp.SIMPLE, "learned": sp.IN_OUT | sp.POLICY_LEARNED}[name]
+    return {"in_out": sp.IN_OUT, "simple": sp.SIMPLE, "learned": sp.IN_OUT | sp.POLICY_LEARNED,
+            "full_weak": sp.IN_FULL | sp.OUT_WEAK, "approx4": sp.approx(4)}[name]
 
 
 def run_reference(args, wl):
