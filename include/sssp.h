@@ -94,6 +94,9 @@ enum {
   SSSP_FRONTIER_AUTO = 1u << 18    /* dense when |F| > n/8, else sparse */
 };
 
+/* Criterion mask of APPROX with recomputation period k (1..63). */
+#define SSSP_APPROX_K(k) (SSSP_APPROX | (((uint32_t)(k) & 63u) << SSSP_APPROX_K_SHIFT))
+
 /* sssp_graph_create build flags. */
 enum { SSSP_GRAPH_REVERSE = 1u << 0 /* also build the in-edge CSR */ };
 
@@ -250,7 +253,6 @@ sssp_status sssp_batch_autotune(sssp_batch* b, void* stream, uint32_t* bpg_out, 
  *   log2(n)/32, (m/n)/32, S'/(1+F')
  * with E', S', F' the relaxed edges, settled vertices and fringe size of the
  * previous phase and k the phase index. */
-#define SSSP_APPROX_K(k) (SSSP_APPROX | (((uint32_t)(k) & 63u) << SSSP_APPROX_K_SHIFT))
 #define SSSP_POLICY_FEATURES 8
 #define SSSP_POLICY_ARMS 4
 #define SSSP_POLICY_WEIGHTS 1476
@@ -330,7 +332,7 @@ sssp_status sssp_solve_noalloc(uint32_t n, uint64_t m, const uint64_t* row_offse
  * 256ths of n (a refill scans all n vertex records, which pays off only for a
  * fringe that is a sizeable share of the graph; 0 = no such condition).
  * Applies to launches made after the call; sssp_set_tuning(NULL) restores the
-  * defaults (4096, 0, 0, 2048, 8192, 0, 32). */
+ * defaults (4096, 0, 0, 2048, 8192, 0, 32). */
 typedef struct {
   uint32_t solo_max_frontier;
   uint32_t batch_blocks_per_solve;
