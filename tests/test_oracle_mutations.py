@@ -23,6 +23,12 @@ MUTANTS = {
     "in_full_uses_out_min": ("c = sat_add(c, w64(g->in_st[x]));", "c = sat_add(c, w64(g->out_st[x]));"),
     "out_weak_drops_second_edge": ("if (which == ORC_OUT_WEAK) c = sat_add(c, w64(g->out_st[x]));",
                                    "if (which == ORC_OUT_WEAK) c = c;"),
+    "in_full_drops_unexplored_term": ("if (which == ORC_IN_FULL && g->st[x] == ST_U)    /* two edges outside S */\n            c = sat_add(",
+                                      "if (0)\n            c = sat_add("),
+    "in_full_term_for_fringe_sources": ("if (which == ORC_IN_FULL && g->st[x] == ST_U)    /* two edges outside S */",
+                                        "if (which == ORC_IN_FULL && g->st[x] != ST_S)    /* two edges outside S */"),
+    "out_weak_term_for_fringe_targets": ("if (g->st[x] == ST_U) {\n            if (which == ORC_OUT_WEAK)",
+                                         "if (g->st[x] != ST_S) {\n            if (which == ORC_OUT_WEAK)"),
     "heap_wrong_child": ("h->a[r].key < h->a[l].key) c = r;", "h->a[r].key > h->a[l].key) c = r;"),
     "new_vertex_not_queued": ("g.st[t] = ST_F; Fn[nFn++] = t;", "g.st[t] = ST_F;"),
     "sum_f_off_by_one": ("sumF += nF;", "sumF += nF - 1;"),
