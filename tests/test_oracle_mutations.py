@@ -29,6 +29,7 @@ MUTANTS = {
                                         "if (which == ORC_IN_FULL && g->st[x] != ST_S)    /* two edges outside S */"),
     "out_weak_term_for_fringe_targets": ("if (g->st[x] == ST_U) {\n            if (which == ORC_OUT_WEAK)",
                                          "if (g->st[x] != ST_S) {\n            if (which == ORC_OUT_WEAK)"),
+    "dijk_tie_takes_queue_order": ("(d_out[v] == minD && v < argmin)", "(d_out[v] == minD && v > argmin)"),
     "heap_wrong_child": ("h->a[r].key < h->a[l].key) c = r;", "h->a[r].key > h->a[l].key) c = r;"),
     "new_vertex_not_queued": ("g.st[t] = ST_F; Fn[nFn++] = t;", "g.st[t] = ST_F;"),
     "sum_f_off_by_one": ("sumF += nF;", "sumF += nF - 1;"),
