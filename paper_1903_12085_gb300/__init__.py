@@ -10,7 +10,7 @@ Names follow the C ABI::
     g = Graph(n, row_off, col, w, reverse=True)      # sssp_graph_create
     dist, phases = solve(g, source, IN_STATIC | OUT_STATIC)   # sssp_solve
     dist, stats, settle, trace = solve_trace(g, source, crit)  # sssp_solve_trace
-    phases = solve_batch([g, ...], [s, ...], crit, outs)       # sssp_solve_batch
+    outs, phases = solve_batch([g, ...], [s, ...], crit)      # sssp_solve_batch
 """
 from __future__ import annotations
 
@@ -31,6 +31,13 @@ IN_FULL = 1 << 4
 OUT_WEAK = 1 << 5
 DIJK = 1 << 6
 APPROX = 1 << 9
+APPROX_K_SHIFT = 10
+POLICY_LEARNED = 1 << 16
+FRONTIER_DENSE = 1 << 17
+FRONTIER_AUTO = 1 << 18
+GRAPH_REVERSE = 1 << 0
+IN_OUT = IN_STATIC | OUT_STATIC
+SIMPLE = IN_SIMPLE | OUT_SIMPLE
 
 
 def approx(k: int) -> int:
@@ -38,13 +45,7 @@ def approx(k: int) -> int:
     every k-th phase (1 <= k <= 63)."""
     if not 1 <= k <= 63:
         raise ValueError("k must be in 1..63")
-    return APPROX | (k << 10)
-POLICY_LEARNED = 1 << 16
-FRONTIER_DENSE = 1 << 17
-FRONTIER_AUTO = 1 << 18
-GRAPH_REVERSE = 1 << 0
-IN_OUT = IN_STATIC | OUT_STATIC
-SIMPLE = IN_SIMPLE | OUT_SIMPLE
+    return APPROX | (k << APPROX_K_SHIFT)
 
 STATUS = {0: "SSSP_OK", 1: "SSSP_ERR_INVALID_ARG", 2: "SSSP_ERR_OUT_OF_MEMORY", 3: "SSSP_ERR_CUDA",
           4: "SSSP_ERR_TIMEOUT", 5: "SSSP_ERR_INTERNAL", 6: "SSSP_ERR_UNSUPPORTED"}
@@ -214,8 +215,9 @@ class Graph:
         return cls(g.n, g.row_off, g.col, g.w, reverse=reverse, stream=stream)
 
     def device_arrays(self):
-        """Preprocessed device arrays as torch tensors (views, no copy)."""
-        torch = _torch()
+        """Device addresses (ints) of the preprocessed arrays held by the
+        handle: row_off, edges, out_min, in_min, rrow_off, redges (the last
+        two 0 without the reverse CSR); valid until close()."""
         ptrs = [ctypes.c_void_p() for _ in range(6)]
         _check(lib().sssp_graph_device_arrays(self.handle, *[ctypes.byref(x) for x in ptrs]))
         return {name: p.value for name, p in zip(["row_off", "edges", "out_min", "in_min", "rrow_off", "redges"], ptrs)}
@@ -233,9 +235,17 @@ class Graph:
 
 
 def _dist_buffer(n, out):
-    torch = _torch()
+    """``out`` if it holds at least n 8-byte words, a new CUDA int64 tensor of
+    n if it is None."""
     if out is None:
-        out = torch.empty(n, dtype=torch.int64, device="cuda")
+        torch = _torch()
+        return torch.empty(n, dtype=torch.int64, device="cuda")
+    if isinstance(out, np.ndarray):
+        words = out.nbytes // 8 if out.flags.c_contiguous else -1
+    else:
+        words = out.numel() * out.element_size() // 8 if out.is_contiguous() else -1
+    if words < n:
+        raise ValueError(f"distance buffer must be a contiguous buffer of at least {n} 8-byte words")
     return out
 
 

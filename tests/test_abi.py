@@ -50,3 +50,24 @@ def test_product_path_does_not_touch_oracle():
             text = open(path).read()
             for bad in ("import oracle", "from oracle", "liboracle", "oracle.c"):
                 assert bad not in text, (path, bad)
+
+
+def test_binding_rejects_short_distance_buffers():
+    """The binding checks a caller's distance buffer before passing its address
+    (the C ABI cannot see the size): too short or strided buffers raise."""
+    import numpy as np
+
+    import paper_1903_12085_gb300 as sp
+
+    ok = np.zeros(10, np.uint64)
+    assert sp._dist_buffer(10, ok) is ok
+    assert sp._dist_buffer(5, ok) is ok
+    with pytest.raises(ValueError):
+        sp._dist_buffer(11, ok)
+    with pytest.raises(ValueError):
+        sp._dist_buffer(5, np.zeros(20, np.uint64)[::2])
+    with pytest.raises(ValueError):
+        sp._dist_buffer(10, np.zeros(10, np.uint32))
+    assert sp.approx(4) == sp.APPROX | (4 << 10)
+    with pytest.raises(ValueError):
+        sp.approx(0)
