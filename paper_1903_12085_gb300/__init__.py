@@ -361,6 +361,9 @@ def solve_batch(graphs, sources, criterion: int = IN_OUT, outs=None, stream=None
     torch = _torch()
     if outs is None:
         outs = [torch.empty(g.n, dtype=torch.int64, device="cuda") for g in graphs]
+    if len(outs) != len(graphs) or len(sources) != len(graphs):
+        raise ValueError("graphs, sources and outs must have the same length")
+    outs = [_dist_buffer(g.n, o) for g, o in zip(graphs, outs)]
     src = np.ascontiguousarray(sources, dtype=np.uint32)
     phases = np.zeros(len(graphs), np.uint64)
     _check(lib().sssp_solve_batch(_ptr_array(graphs), _ptr(src), len(graphs), int(criterion), _ptr_array(outs),
@@ -377,6 +380,9 @@ class Batch:
         self.graphs = list(graphs)
         self.outs = outs if outs is not None else [torch.empty(g.n, dtype=torch.int64, device="cuda")
                                                    for g in self.graphs]
+        if len(self.outs) != len(self.graphs) or len(sources) != len(self.graphs):
+            raise ValueError("graphs, sources and outs must have the same length")
+        self.outs = [_dist_buffer(g.n, o) for g, o in zip(self.graphs, self.outs)]
         self.phases = torch.zeros(len(self.graphs), dtype=torch.int64, device="cuda")
         src = np.ascontiguousarray(sources, dtype=np.uint32)
         h = ctypes.c_void_p()

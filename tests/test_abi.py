@@ -71,3 +71,17 @@ def test_binding_rejects_short_distance_buffers():
     assert sp.approx(4) == sp.APPROX | (4 << 10)
     with pytest.raises(ValueError):
         sp.approx(0)
+
+
+def test_binding_checks_batch_lengths_before_any_call():
+    import types
+
+    import numpy as np
+
+    import paper_1903_12085_gb300 as sp
+
+    g = types.SimpleNamespace(n=3)
+    with pytest.raises(ValueError):
+        sp.solve_batch([g], [0, 1], outs=[np.zeros(3, np.uint64)])
+    with pytest.raises(ValueError):
+        sp.solve_batch([g, g], [0, 1], outs=[np.zeros(3, np.uint64), np.zeros(2, np.uint64)])
