@@ -1,5 +1,6 @@
 // capi.cu -- error reporting and small utilities behind the C ABI.
 #include <atomic>
+#include <cstdarg>
 #include <cstdio>
 
 #include "engine.h"
@@ -49,14 +50,19 @@ bool is_device_pointer(const void* p) {
 }
 
 int sm_count() {
-  static int cached = 0;
-  if (!cached) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&cached, cudaDevAttrMultiProcessorCount, dev);
-    if (cached <= 0) cached = 1;
+  // per device ordinal (a process may switch devices between calls)
+  constexpr int kMaxDevices = 64;
+  static std::atomic<int> cached[kMaxDevices];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const int slot = dev >= 0 && dev < kMaxDevices ? dev : 0;
+  int c = cached[slot].load();
+  if (c <= 0) {
+    cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev);
+    if (c <= 0) c = 1;
+    cached[slot].store(c);
   }
-  return cached;
+  return c;
 }
 
 }  // namespace sssp
@@ -72,18 +78,17 @@ __global__ void k_selftest_wait(const unsigned int* flag, unsigned long long lim
 
 extern "C" sssp_status sssp_selftest_wait(uint64_t limit_ns) {
   sssp::clear_error();
-  unsigned int* flag = nullptr;
-  int* err = nullptr;
+  unsigned int* words = nullptr;  // [0] the flag nothing writes, [1] the error word
   int herr = 0;
-  SSSP_CUDA_TRY(cudaMalloc(&flag, sizeof(unsigned int)));
-  SSSP_CUDA_TRY(cudaMalloc(&err, sizeof(int)));
-  SSSP_CUDA_TRY(cudaMemset(flag, 0, sizeof(unsigned int)));
-  SSSP_CUDA_TRY(cudaMemset(err, 0, sizeof(int)));
-  sssp::k_selftest_wait<<<1, 32>>>(flag, limit_ns, err);
-  SSSP_CUDA_TRY(cudaGetLastError());
-  SSSP_CUDA_TRY(cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost));
-  cudaFree(flag);
-  cudaFree(err);
+  SSSP_CUDA_TRY(cudaMalloc(&words, 2 * sizeof(unsigned int)));
+  cudaError_t e = cudaMemset(words, 0, 2 * sizeof(unsigned int));
+  if (e == cudaSuccess) {
+    sssp::k_selftest_wait<<<1, 32>>>(words, limit_ns, reinterpret_cast<int*>(words + 1));
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(&herr, words + 1, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(words);
+  if (e != cudaSuccess) return sssp::fail(SSSP_ERR_CUDA, "self-test wait: %s", cudaGetErrorString(e));
   if (herr != 0) return sssp::fail((sssp_status)herr, "bounded wait gave up as designed");
   return SSSP_OK;
 }
