@@ -16,8 +16,9 @@
  *                     per-phase criterion mask.  Every phase evaluates the
  *                     chosen criteria on the state at the start of the phase,
  *                     settles ALL fringe vertices that satisfy one of them
- *                     (Section 4: "all vertices fulfilling the criteria prior
- *                     to a phase are selected"), then relaxes their out-edges.
+ *                     (the phase model of Section 4's simulations, where
+ *                     every vertex meeting the criterion at the start of a
+ *                     phase is taken), then relaxes their out-edges.
  *
  * Criterion bits (a disjunction of every bit set), with the equations they
  * restate:
