@@ -85,3 +85,21 @@ def test_binding_checks_batch_lengths_before_any_call():
         sp.solve_batch([g], [0, 1], outs=[np.zeros(3, np.uint64)])
     with pytest.raises(ValueError):
         sp.solve_batch([g, g], [0, 1], outs=[np.zeros(3, np.uint64), np.zeros(2, np.uint64)])
+
+
+def test_policy_features_follow_the_documented_formula():
+    """sssp_policy_features (a host function; the engine evaluates the same
+    code per phase) against the eight features listed in include/sssp.h."""
+    import numpy as np
+
+    import paper_1903_12085_gb300 as sp
+
+    cases = [(1, 16384, 131072, 1, 0, 0, 0), (5000, 1 << 22, 1 << 26, 37, 81234, 4021, 6123),
+             (1 << 20, 1 << 24, 1 << 28, 1085, 3 << 20, 9 << 10, 1 << 21), (0, 7, 0, 2, 0, 0, 0)]
+    for F, n, m, k, e, s, f in cases:
+        want = np.array([np.log2(1 + F) / 24, F / n, np.log2(1 + e) / 24, np.log2(1 + s) / 24,
+                         np.log2(1 + k) / 16, np.log2(n) / 32, (m / n) / 32, s / (1 + f)])
+        got = sp.policy_features(F, n, m, k, e, s, f).astype(np.float64)
+        assert np.allclose(got, want, rtol=1e-5, atol=1e-6), (got, want)
+    with pytest.raises(sp.SsspError):
+        sp.policy_features(1, 0, 0, 1, 0, 0, 0)  # n = 0 is rejected
