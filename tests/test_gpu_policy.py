@@ -161,4 +161,5 @@ def test_trained_policy_gain(capsys):
             print(f"  {r[0]:24s} {r[1]:9.3f} {r[2]:7d} {r[3]:9.3f} {r[4]:7d} {r[1] / r[3]:6.2f}x")
     total_fix = sum(r[1] for r in rows)
     total_learn = sum(r[3] for r in rows)
-    assert total_learn <= 1.10 * total_fix
+    assert total_learn <= 1.10 * total_fix  # never much worse in total
+    assert max(r[1] / r[3] for r in rows) >= 1.05  # and a real gain on some held-out graph
