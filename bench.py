@@ -492,6 +492,7 @@ def main():
                        "queries_per_s": tot["solves"] / (total_ms * 1e-3),
                        "us_per_phase": 1e3 * local_ms / phases, "sum_frontier_per_solve": tot["sum_f"] / tot["solves"],
                        "sum_queued_per_solve": tot["sum_q"] / tot["solves"],
+                       "median_ms_per_step_rank0": statistics.median(step_ms),
                        "prep_ms": prep_ms, "l2": "flushed between steps (2x L2 buffer written)",
                        "parallelism": f"replicas x{ws}", "batch_autotune": batch_tune},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
