@@ -1,6 +1,6 @@
 """Phase-count study with the CPU oracle (analysis; test infrastructure only).
 
-    python oracle/phase_study.py [--samples S] [--jobs J]
+    python oracle/phase_study.py [--samples S] [--jobs J] [--approx]
 
 The paper's simulation section counts, for every criterion, the phases the
 generic algorithm needs to settle all reachable vertices and the sum of |F|
@@ -89,11 +89,59 @@ def fit(ns, ys, log_form: bool):
     return float(a), float(b), float(c)
 
 
+# APPROX(k) sweep (the approximate minima of Section 3's closing remark): the
+# static criteria, APPROX(k) for growing k, and IN (full) | OUT-WEAK, which
+# APPROX(1) equals; uniform family only.
+APPROX_KS = [1, 2, 4, 8, 16, 32]
+APPROX_OUT = os.path.join(HERE, "approx_study.json")
+
+
+def _run_approx(task):
+    size, sample = task
+    sys.path.insert(0, ROOT)
+    import oracle
+    g, s = _graph("uniform", size, sample)
+    d = oracle.dijkstra(g, s)
+    out = {"size": size, "n": g.n, "sample": sample}
+    crits = [("IN-STATIC|OUT-STATIC", 3), ("IN|OUT-WEAK", 16 | 32)] + [(f"APPROX({k})", oracle.approx(k))
+                                                                        for k in APPROX_KS]
+    for name, mask in crits:
+        sim = oracle.simulate(g, s, mask, dist_ref=d)
+        out[name] = (sim.phases, sim.sum_f)
+    return out
+
+
+def approx_main(samples: int, jobs: int):
+    sizes = [1 << e for e in range(10, 19)]
+    tasks = sorted([(z, s) for z in sizes for s in range(samples)], key=lambda t: -t[0])
+    with mp.get_context("spawn").Pool(jobs) as pool:
+        rows = list(pool.imap_unordered(_run_approx, tasks))
+    names = ["IN-STATIC|OUT-STATIC"] + [f"APPROX({k})" for k in reversed(APPROX_KS)] + ["IN|OUT-WEAK"]
+    result = {"samples": samples, "rows": rows, "fits": {}}
+    ns = [sum(r["n"] for r in rows if r["size"] == z) / samples for z in sizes]
+    for name in names:
+        ph = [sum(r[name][0] for r in rows if r["size"] == z) / samples for z in sizes]
+        result["fits"][name] = {"phases": fit(ns, ph, False), "mean_phases": ph, "n": ns}
+    with open(APPROX_OUT, "w") as f:
+        json.dump(result, f, indent=1)
+    print("| criterion | phases fit | mean phases at n = 2^10 | at n = 2^18 |")
+    print("|---|---|---:|---:|")
+    for name in names:
+        a, b, c = result["fits"][name]["phases"]
+        ph = result["fits"][name]["mean_phases"]
+        print(f"| {name} | {b:.2f} n^{c:.2f} | {ph[0]:.1f} | {ph[-1]:.1f} |")
+    print("wrote", APPROX_OUT)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--samples", type=int, default=10)
     ap.add_argument("--jobs", type=int, default=max(1, (os.cpu_count() or 2) - 1))
+    ap.add_argument("--approx", action="store_true", help="run the APPROX(k) sweep instead")
     args = ap.parse_args()
+    if args.approx:
+        approx_main(args.samples, args.jobs)
+        return
     tasks = [("uniform", n, s) for n in uniform_sizes() for s in range(args.samples)]
     tasks += [("kronecker", k, s) for k in kron_scales() for s in range(args.samples)]
     tasks.sort(key=lambda t: -(t[1] if t[0] == "uniform" else 2 ** t[1]))

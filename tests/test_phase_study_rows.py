@@ -61,3 +61,23 @@ def test_gpu_traces_reproduce_the_study():
             checked += 1
         G.close()
     assert checked == 7 * len(rows)
+
+
+def test_stored_approx_rows_are_the_oracles():
+    """The APPROX(k) sweep (oracle/approx_study.json): stored rows re-computed
+    by the oracle; on every row APPROX(1) equals IN (full) | OUT-WEAK; the mean
+    phase count never falls as k grows and stays at most the static one."""
+    with open(os.path.join(os.path.dirname(oracle.__file__), "approx_study.json")) as f:
+        study = json.load(f)
+    rows = study["rows"]
+    for r in rows:
+        assert r["APPROX(1)"] == r["IN|OUT-WEAK"], r["size"]
+    for r in [r for r in rows if r["size"] <= 2048 and r["sample"] < 2]:
+        g, s = ps._graph("uniform", r["size"], r["sample"])
+        d = oracle.dijkstra(g, s)
+        for k in ps.APPROX_KS:
+            sim = oracle.simulate(g, s, oracle.approx(k), dist_ref=d)
+            assert [sim.phases, sim.sum_f] == r[f"APPROX({k})"], (r["size"], k)
+    means = [np.mean([r[f"APPROX({k})"][0] for r in rows]) for k in ps.APPROX_KS]
+    static = np.mean([r["IN-STATIC|OUT-STATIC"][0] for r in rows])
+    assert all(a <= b for a, b in zip(means, means[1:])) and means[-1] <= static
