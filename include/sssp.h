@@ -26,6 +26,9 @@
  *     frees it in the matching destroy call.
  *   - Solves on one graph handle share its workspace: do not run two solves
  *     on the same handle at the same time (use sssp_solve_batch instead).
+ *   - One device per process: the first solve sets the solve kernels' launch
+ *     attributes for the device that is current then.  Make that first solve
+ *     from one thread before others start solving.
  */
 #ifndef SSSP_GB300_H
 #define SSSP_GB300_H
