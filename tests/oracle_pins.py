@@ -9,7 +9,6 @@ broken copies of the oracle to show that plausible mistakes are caught.
 """
 from __future__ import annotations
 
-import itertools
 import json
 import os
 from collections import deque
