@@ -214,7 +214,7 @@ def run_reference(args, wl):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": wl.name, "solver": "oracle binary-heap Dijkstra, 1 host core"},
         "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle",
-                         "sample": f"{args.steps} whole solves of {wl.name}"},
+                         "sample": f"{args.steps} whole solves of {wl.name}", **host_info()},
         "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
@@ -232,7 +232,14 @@ def cpu_baseline(wl, budget_s=12.0):
         edges += int(g.outdeg()[d != oracle.INF].sum())
         count += 1
     return {"value": edges / t / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
-            "sample": f"{count} whole binary-heap Dijkstra solves of {wl.name} ({t:.1f} s, 1 thread)"}
+            "sample": f"{count} whole binary-heap Dijkstra solves of {wl.name} ({t:.1f} s, 1 thread)",
+            **host_info()}
+
+
+def host_info():
+    """The host the CPU baseline ran on (it uses one of these cores)."""
+    import platform
+    return {"host_cpus": os.cpu_count(), "host_arch": platform.machine()}
 
 
 def main():
