@@ -127,6 +127,13 @@ extern "C" sssp_status sssp_solve_noalloc(uint32_t n, uint64_t m, const uint64_t
   if ((criterion & SSSP_CRITERIA_MASK) == 0 || (criterion & ~allowed))
     return fail(SSSP_ERR_UNSUPPORTED, "sssp_solve_noalloc takes IN_STATIC, OUT_STATIC and DIJK only (mask 0x%x)",
                 criterion);
+  // The solve reads row_offsets and dist_out as 8-byte words and edges as
+  // 8-byte {target, cost} pairs: a buffer that does not start on an 8-byte
+  // boundary (a tensor slice at an odd 4-byte offset, say) would fault on the
+  // GPU, so it is rejected here, before any CUDA call.
+  if ((reinterpret_cast<uintptr_t>(row_offsets) & 7u) || (reinterpret_cast<uintptr_t>(edges) & 7u) ||
+      (reinterpret_cast<uintptr_t>(dist_out) & 7u))
+    return fail(SSSP_ERR_INVALID_ARG, "sssp_solve_noalloc: row_offsets, edges and dist_out must be 8-byte aligned");
   if (!row_offsets || !dist_out || (m > 0 && !edges) || !is_device_pointer(row_offsets) ||
       !is_device_pointer(dist_out) || (m > 0 && !is_device_pointer(edges)))
     return fail(SSSP_ERR_INVALID_ARG, "sssp_solve_noalloc: row_offsets, edges and dist_out must be device memory");
