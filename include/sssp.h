@@ -26,9 +26,11 @@
  *     frees it in the matching destroy call.
  *   - Solves on one graph handle share its workspace: do not run two solves
  *     on the same handle at the same time (use sssp_solve_batch instead).
- *   - One device per process: the first solve sets the solve kernels' launch
- *     attributes for the device that is current then.  Make that first solve
- *     from one thread before others start solving.
+ *   - Every call works on the CUDA device that is current on the calling
+ *     thread.  The first solve on a device sets the solve kernels' launch
+ *     attributes for that device, under a lock, so threads may make their
+ *     first solves concurrently and a process may use several devices.
+ *     Handles belong to the device they were created on.
  */
 #ifndef SSSP_GB300_H
 #define SSSP_GB300_H
@@ -295,6 +297,8 @@ sssp_status sssp_mlp_adam(float* w, const float* grad, float* m1, float* m2, uin
  *   row_offsets  uint64[n+1] device memory (as in sssp_graph_create)
  *   edges        uint32 pairs {target, cost}, 2*m words, device memory; rows
  *                need not be sorted
+ *   (row_offsets, edges and dist_out must start on an 8-byte boundary:
+ *   anything else is rejected with SSSP_ERR_INVALID_ARG before any CUDA call)
  *   criterion    SSSP_IN_STATIC, SSSP_OUT_STATIC and/or SSSP_DIJK (plus the
  *                frontier options); other criteria -> SSSP_ERR_UNSUPPORTED
  *   dist_out     uint64[n] device memory, receives the distances
@@ -348,6 +352,18 @@ typedef struct {
 } sssp_tuning;
 sssp_status sssp_set_tuning(const sssp_tuning* t);
 sssp_status sssp_get_tuning(sssp_tuning* t);
+
+/* Device memory the library holds, and an optional cap on it (a library
+ * feature with no counterpart in the paper).  Every device allocation of the
+ * library (graph handles, solve workspaces, batches, the policy network and
+ * the temporaries of preprocessing and training) is counted, over all devices
+ * of the process.  With a cap (bytes > 0) a request that would take the total
+ * above it fails with SSSP_ERR_OUT_OF_MEMORY before cudaMalloc is called, and
+ * the failing call frees everything it had taken, exactly as for a failed
+ * cudaMalloc; 0 removes the cap (the default).  sssp_solve_noalloc allocates
+ * nothing and is not affected.  Applies to calls made after it. */
+sssp_status sssp_set_device_memory_limit(uint64_t bytes);
+sssp_status sssp_device_memory_in_use(uint64_t* bytes);
 
 /* Upper bound, in nanoseconds, on any single in-kernel wait (grid barrier,
  * work queue).  A wait that runs out sets SSSP_ERR_TIMEOUT and the kernel

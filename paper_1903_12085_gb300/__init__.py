@@ -90,6 +90,8 @@ def lib():
             "sssp_batch_create": [p, p, u32, u32, p, p, p, ctypes.POINTER(p)],
             "sssp_batch_launch": [p, p],
             "sssp_set_wait_limit_ns": [u64],
+            "sssp_set_device_memory_limit": [u64],
+            "sssp_device_memory_in_use": [p],
             "sssp_selftest_wait": [u64],
             "sssp_solve_noalloc": [u32, u64, p, p, u32, u32, p, p, p],
             "sssp_batch_autotune": [p, p, p, p],
@@ -146,6 +148,19 @@ def version() -> str:
 
 def set_wait_limit_ns(ns: int):
     _check(lib().sssp_set_wait_limit_ns(int(ns)))
+
+
+def set_device_memory_limit(nbytes: int):
+    """sssp_set_device_memory_limit: cap on the device memory the library
+    allocates (0 = no cap)."""
+    _check(lib().sssp_set_device_memory_limit(int(nbytes)))
+
+
+def device_memory_in_use() -> int:
+    """sssp_device_memory_in_use: bytes of device memory the library holds."""
+    b = ctypes.c_uint64()
+    _check(lib().sssp_device_memory_in_use(ctypes.byref(b)))
+    return b.value
 
 
 def selftest_wait(limit_ns: int) -> int:
@@ -281,12 +296,30 @@ def solve_trace(g: Graph, source: int, criterion: int = IN_OUT, out=None, trace_
 NOALLOC_MAX_VERTICES = 1 << 19
 
 
+def _noalloc_inputs(n, row_off, edges):
+    """Checks what the C ABI cannot see about the caller's CSR tensors: device,
+    element size, contiguity and length (the library reads n+1 offsets and m
+    {target, cost} pairs through raw pointers).  Raises ValueError."""
+    for name, t, size in (("row_off", row_off, 8), ("edges", edges, 4)):
+        if isinstance(t, np.ndarray) or not getattr(t, "is_cuda", False):
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if t.element_size() != size or t.is_floating_point() or t.is_complex():
+            raise ValueError(f"{name} must hold {8 * size}-bit integers")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    if row_off.numel() < n + 1:
+        raise ValueError(f"row_off needs at least n+1 = {n + 1} entries, it has {row_off.numel()}")
+    if edges.numel() % 2:
+        raise ValueError("edges must hold {target, cost} pairs (an even number of 32-bit words)")
+
+
 def solve_noalloc(n: int, row_off, edges, source: int, criterion: int = IN_OUT, out=None, stream=None):
     """sssp_solve_noalloc: a solve that allocates no device memory.  ``row_off``
     (int64/uint64, n+1) and ``edges`` (int32/uint32 pairs {target, cost}, 2*m)
     are CUDA tensors; ``out`` a CUDA int64 tensor of n (allocated here by torch
     if None -- pass it in to keep the whole call allocation-free).  Returns
     (dist, phases)."""
+    _noalloc_inputs(n, row_off, edges)
     out = _dist_buffer(n, out)
     phases = ctypes.c_uint64()
     m = int(edges.numel()) // 2

@@ -80,14 +80,17 @@ extern "C" sssp_status sssp_selftest_wait(uint64_t limit_ns) {
   sssp::clear_error();
   unsigned int* words = nullptr;  // [0] the flag nothing writes, [1] the error word
   int herr = 0;
-  SSSP_CUDA_TRY(cudaMalloc(&words, 2 * sizeof(unsigned int)));
+  {
+    sssp_status s = sssp::dev_alloc(&words, 2);
+    if (s != SSSP_OK) return s;
+  }
   cudaError_t e = cudaMemset(words, 0, 2 * sizeof(unsigned int));
   if (e == cudaSuccess) {
     sssp::k_selftest_wait<<<1, 32>>>(words, limit_ns, reinterpret_cast<int*>(words + 1));
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaMemcpy(&herr, words + 1, sizeof(int), cudaMemcpyDeviceToHost);
-  cudaFree(words);
+  sssp::dev_free(words);
   if (e != cudaSuccess) return sssp::fail(SSSP_ERR_CUDA, "self-test wait: %s", cudaGetErrorString(e));
   if (herr != 0) return sssp::fail((sssp_status)herr, "bounded wait gave up as designed");
   return SSSP_OK;

@@ -39,7 +39,9 @@
 // Phase control: the phase that settles the source is phase 1; the loop ends
 // when the next queue is empty.
 #include <algorithm>
+#include <atomic>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "engine.h"
@@ -1685,20 +1687,46 @@ __global__ void __launch_bounds__(kThreads) k_solve_batch(const BatchItem* items
 
 namespace {
 
-int g_blocks_per_sm = 0;
+// Co-resident blocks per SM of the solve kernels, per device ordinal (0 = not
+// set up yet).  The first solve on a device sets the kernels' shared-memory
+// attribute and measures the occupancy with that device current; the mutex
+// makes concurrent first solves from several threads safe.
+constexpr int kMaxDevices = 64;
+std::atomic<int> g_blocks_per_sm[kMaxDevices];
+std::mutex g_attr_mu;
+
+int current_device() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  return dev;
+}
 
 sssp_status ensure_kernel_attrs() {
-  static bool done = false;
-  if (done) return SSSP_OK;
+  const int dev = current_device();
+  if (dev < 0 || dev >= kMaxDevices) return fail(SSSP_ERR_CUDA, "no usable current CUDA device (ordinal %d)", dev);
+  if (g_blocks_per_sm[dev].load() > 0) return SSSP_OK;
+  std::lock_guard<std::mutex> lock(g_attr_mu);
+  if (g_blocks_per_sm[dev].load() > 0) return SSSP_OK;
   SSSP_CUDA_TRY(cudaFuncSetAttribute(k_solve_grid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes));
   SSSP_CUDA_TRY(cudaFuncSetAttribute(k_solve_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes));
   int a = 0, b = 0;
   SSSP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_solve_grid, kThreads, kSmemBytes));
   SSSP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_solve_batch, kThreads, kSmemBytes));
-  g_blocks_per_sm = std::min(a, b);
-  if (g_blocks_per_sm < 1) return fail(SSSP_ERR_CUDA, "solve kernel cannot be resident");
-  done = true;
+  const int per_sm = std::min(a, b);
+  if (per_sm < 1) return fail(SSSP_ERR_CUDA, "solve kernel cannot be resident");
+  g_blocks_per_sm[dev].store(per_sm);
   return SSSP_OK;
+}
+
+// Co-resident blocks of the solve kernels on the current device (after
+// ensure_kernel_attrs succeeded on it).
+uint32_t resident_blocks() {
+  const int dev = current_device();
+  const int per_sm = dev >= 0 && dev < kMaxDevices ? g_blocks_per_sm[dev].load() : 0;
+  return (uint32_t)std::max(1, per_sm * sm_count());
 }
 
 sssp_status check_crit(const sssp_graph* g, uint32_t crit) {
@@ -1719,16 +1747,10 @@ sssp_status check_crit(const sssp_graph* g, uint32_t crit) {
   return SSSP_OK;
 }
 
-template <class T>
-sssp_status dev_alloc(T** p, size_t count) {
-  SSSP_CUDA_TRY(cudaMalloc(p, std::max<size_t>(count, 1) * sizeof(T)));
-  return SSSP_OK;
-}
-
 // Blocks for a single solve: enough to cover the vertices, at most all
 // co-resident blocks.
 int blocks_for(uint32_t n) {
-  const int max_blocks = g_blocks_per_sm * sm_count();
+  const int max_blocks = (int)resident_blocks();
   const uint64_t want = grid_blocks() ? grid_blocks() : ((uint64_t)n + kTile - 1) / kTile;
   return (int)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)max_blocks));
 }
@@ -1737,21 +1759,21 @@ int blocks_for(uint32_t n) {
 
 void workspace_free(Workspace* ws) {
   if (!ws) return;
-  cudaFree(ws->vrec);
-  cudaFree(ws->status);
-  cudaFree(ws->q0);
-  cudaFree(ws->q1);
-  cudaFree(ws->sp);
-  cudaFree(ws->cur_out);
-  cudaFree(ws->cur_in);
-  cudaFree(ws->im_dyn);
-  cudaFree(ws->tile_owner);
-  cudaFree(ws->im_full);
-  cudaFree(ws->apx_in);
-  cudaFree(ws->apx_out);
-  cudaFree(ws->fresh);
-  cudaFree(ws->dist);
-  cudaFree(ws->ctl);
+  dev_free(ws->vrec);
+  dev_free(ws->status);
+  dev_free(ws->q0);
+  dev_free(ws->q1);
+  dev_free(ws->sp);
+  dev_free(ws->cur_out);
+  dev_free(ws->cur_in);
+  dev_free(ws->im_dyn);
+  dev_free(ws->tile_owner);
+  dev_free(ws->im_full);
+  dev_free(ws->apx_in);
+  dev_free(ws->apx_out);
+  dev_free(ws->fresh);
+  dev_free(ws->dist);
+  dev_free(ws->ctl);
   cudaFreeHost(ws->ctl_host);
   delete ws;
 }
@@ -1836,10 +1858,12 @@ sssp_status solve_one(sssp_graph* g, uint32_t source, uint32_t crit, uint64_t* d
 
   const bool dist_dev = is_device_pointer(dist_out);
   const bool sp_dev = settle_phase && is_device_pointer(settle_phase);
-  uint32_t* sp_buf = nullptr;
-  sssp_phase_record* tr_buf = nullptr;
-  if (settle_phase && !sp_dev) SSSP_CUDA_TRY(cudaMallocAsync(&sp_buf, g->n * sizeof(uint32_t), st));
-  if (trace && trace_cap) SSSP_CUDA_TRY(cudaMallocAsync(&tr_buf, trace_cap * sizeof(sssp_phase_record), st));
+  TmpBuf<uint32_t> sp_tmp(st);
+  TmpBuf<sssp_phase_record> tr_tmp(st);
+  if (settle_phase && !sp_dev && (s = sp_tmp.alloc(g->n)) != SSSP_OK) return s;
+  if (trace && trace_cap && (s = tr_tmp.alloc(trace_cap)) != SSSP_OK) return s;
+  uint32_t* sp_buf = sp_tmp.p;
+  sssp_phase_record* tr_buf = tr_tmp.p;
 
   SolveParams p;
   memset(&p, 0, sizeof p);
@@ -1870,17 +1894,13 @@ sssp_status solve_one(sssp_graph* g, uint32_t source, uint32_t crit, uint64_t* d
   SSSP_CUDA_TRY(cudaStreamSynchronize(st));
   const Ctl& c = *ws->ctl_host;
   if (c.err != 0) {
-    if (sp_buf) cudaFree(sp_buf);
-    if (tr_buf) cudaFree(tr_buf);
     return fail((sssp_status)c.err, c.err == SSSP_ERR_TIMEOUT ? "an in-kernel wait exceeded its limit"
                                                                : "device-side error %d", c.err);
   }
   if (tr_buf) {
     const uint64_t rec = std::min<uint64_t>(trace_cap, c.phases);
     if (rec) SSSP_CUDA_TRY(cudaMemcpy(trace, tr_buf, rec * sizeof(sssp_phase_record), cudaMemcpyDeviceToHost));
-    SSSP_CUDA_TRY(cudaFree(tr_buf));
   }
-  if (sp_buf) SSSP_CUDA_TRY(cudaFree(sp_buf));
   if (phases_out) *phases_out = c.phases;
   if (stats) {
     stats->phases = c.phases;
@@ -1922,11 +1942,11 @@ void batch_free(sssp_batch* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   for (Workspace* w : b->ws) workspace_free(w);
-  cudaFree(b->items);
-  cudaFree(b->next);
-  cudaFree(b->gslots);
-  cudaFree(b->err);
-  if (b->own_phases) cudaFree(b->phases);
+  dev_free(b->items);
+  dev_free(b->next);
+  dev_free(b->gslots);
+  dev_free(b->err);
+  if (b->own_phases) dev_free(b->phases);
   delete b;
 }
 
@@ -1961,7 +1981,7 @@ sssp_status batch_build(sssp_graph* const* graphs, const uint32_t* sources, uint
   }
   sssp_status s = ensure_kernel_attrs();
   if (s != SSSP_OK) return s;
-  const uint32_t resident = (uint32_t)(g_blocks_per_sm * sm_count());
+  const uint32_t resident = resident_blocks();
   if (bpg == 0) bpg = 1;
   if (bpg > resident) bpg = resident;
   sssp_batch* b = new (std::nothrow) sssp_batch();
@@ -1991,20 +2011,19 @@ sssp_status batch_build(sssp_graph* const* graphs, const uint32_t* sources, uint
     h[k].source = sources[i];
     h[k].out_index = i;
   }
-  if (cudaMalloc(&b->items, count * sizeof(BatchItem)) != cudaSuccess ||
-      cudaMalloc(&b->next, sizeof(unsigned int)) != cudaSuccess ||
-      cudaMalloc(&b->gslots, std::max<uint32_t>(1, std::min(count, resident)) * sizeof(GroupSlot)) != cudaSuccess ||
-      cudaMalloc(&b->err, sizeof(int)) != cudaSuccess) {
+  if ((s = dev_alloc(&b->items, count)) != SSSP_OK || (s = dev_alloc(&b->next, 1)) != SSSP_OK ||
+      (s = dev_alloc(&b->gslots, std::max<uint32_t>(1, std::min(count, resident)))) != SSSP_OK ||
+      (s = dev_alloc(&b->err, 1)) != SSSP_OK) {
     batch_free(b);
-    return fail(SSSP_ERR_OUT_OF_MEMORY, "device allocation failed");
+    return s;
   }
   if (phases_dev) {
     b->phases = reinterpret_cast<unsigned long long*>(phases_dev);
   } else {
     b->own_phases = true;
-    if (cudaMalloc(&b->phases, count * sizeof(unsigned long long)) != cudaSuccess) {
+    if ((s = dev_alloc(&b->phases, count)) != SSSP_OK) {
       batch_free(b);
-      return fail(SSSP_ERR_OUT_OF_MEMORY, "device allocation failed");
+      return s;
     }
   }
   if (cudaMemcpyAsync(b->items, h.data(), count * sizeof(BatchItem), cudaMemcpyHostToDevice, st) != cudaSuccess ||
@@ -2044,7 +2063,7 @@ sssp_status batch_status(sssp_batch* b) {
 // Blocks per solve for a batch: as many groups as solves while that keeps
 // every resident block busy, fewer (larger) groups for few large solves.
 uint32_t choose_bpg(sssp_graph* const* graphs, uint32_t count) {
-  const uint32_t resident = (uint32_t)(g_blocks_per_sm * sm_count());
+  const uint32_t resident = resident_blocks();
   uint64_t maxn = 0;
   for (uint32_t i = 0; i < count; ++i) maxn = std::max<uint64_t>(maxn, graphs[i]->n);
   const uint32_t bpg = std::max<uint32_t>(1, resident / std::max<uint32_t>(1, count));
@@ -2124,7 +2143,7 @@ extern "C" sssp_status sssp_batch_autotune(sssp_batch* b, void* stream, uint32_t
   clear_error();
   if (!b) return fail(SSSP_ERR_INVALID_ARG, "batch is NULL");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const uint32_t resident = (uint32_t)(g_blocks_per_sm * sm_count());
+  const uint32_t resident = resident_blocks();
   // candidates: 1, 2, 4, ..., all co-resident blocks, and the batch's own
   // choice.  The search starts at the batch's choice and walks up and then
   // down the ladder; a walk stops at the first candidate that is clearly

@@ -324,23 +324,26 @@ int grid_for(uint64_t items, int threads) {
 
 sssp_status exclusive_scan(const uint32_t* in, uint64_t n, uint64_t* out, cudaStream_t st) {
   const uint64_t ntiles = std::max<uint64_t>(1, (n + kScanTile - 1) / kScanTile);
-  uint64_t* tiles = nullptr;
-  SSSP_CUDA_TRY(cudaMallocAsync(&tiles, ntiles * sizeof(uint64_t), st));
+  TmpBuf<uint64_t> tbuf(st);
+  sssp_status s = tbuf.alloc(ntiles);
+  if (s != SSSP_OK) return s;
+  uint64_t* tiles = tbuf.p;
   k_scan_tiles<<<(unsigned)ntiles, kScanThreads, 0, st>>>(in, n, tiles);
   k_scan_tile_sums<<<1, kScanThreads, 0, st>>>(tiles, ntiles);
   k_scan_apply<<<(unsigned)ntiles, kScanThreads, 0, st>>>(in, n, tiles, out);
   SSSP_CUDA_TRY(cudaGetLastError());
-  SSSP_CUDA_TRY(cudaFreeAsync(tiles, st));
   return SSSP_OK;
 }
 
 // Sort every row of (ro, keys) by key.  Temporary buffers come from the stream pool.
 sssp_status sort_rows(const uint64_t* ro, uint32_t n, uint64_t m, unsigned long long* keys, cudaStream_t st) {
   if (m == 0) return SSSP_OK;
-  uint32_t* lists = nullptr;
-  unsigned int* counts = nullptr;
-  SSSP_CUDA_TRY(cudaMallocAsync(&lists, 3ull * n * sizeof(uint32_t), st));
-  SSSP_CUDA_TRY(cudaMallocAsync(&counts, 4 * sizeof(unsigned int), st));
+  TmpBuf<uint32_t> lbuf(st);
+  TmpBuf<unsigned int> cbuf(st);
+  sssp_status s = SSSP_OK;
+  if ((s = lbuf.alloc(3ull * n)) != SSSP_OK || (s = cbuf.alloc(4)) != SSSP_OK) return s;
+  uint32_t* lists = lbuf.p;
+  unsigned int* counts = cbuf.p;
   SSSP_CUDA_TRY(cudaMemsetAsync(counts, 0, 4 * sizeof(unsigned int), st));
   uint32_t *small = lists, *mid = lists + n, *large = lists + 2ull * n;
   k_classify_rows<<<grid_for(n, 256), 256, 0, st>>>(ro, n, small, mid, large, counts);
@@ -353,8 +356,9 @@ sssp_status sort_rows(const uint64_t* ro, uint32_t n, uint64_t m, unsigned long 
   const uint64_t maxdeg = hc[3];
   if (nlarge > 0) {
     k_sort_chunks<<<sm_count() * 4, kSortThreads, 0, st>>>(ro, large, counts + 2, keys);
-    unsigned long long* tmp = nullptr;
-    SSSP_CUDA_TRY(cudaMallocAsync(&tmp, m * sizeof(unsigned long long), st));
+    TmpBuf<unsigned long long> mbuf(st);
+    if ((s = mbuf.alloc(m)) != SSSP_OK) return s;
+    unsigned long long* tmp = mbuf.p;
     unsigned long long *src = keys, *dst = tmp;
     for (uint64_t width = kMidCap; width < maxdeg; width *= 2) {
       k_merge_pass<<<sm_count() * 4, 256, 0, st>>>(ro, large, counts + 2, src, dst, width);
@@ -362,11 +366,8 @@ sssp_status sort_rows(const uint64_t* ro, uint32_t n, uint64_t m, unsigned long 
     }
     if (src != keys) k_copy_rows<<<sm_count() * 4, 256, 0, st>>>(ro, large, counts + 2, src, keys);
     SSSP_CUDA_TRY(cudaGetLastError());
-    SSSP_CUDA_TRY(cudaFreeAsync(tmp, st));
   }
   SSSP_CUDA_TRY(cudaGetLastError());
-  SSSP_CUDA_TRY(cudaFreeAsync(lists, st));
-  SSSP_CUDA_TRY(cudaFreeAsync(counts, st));
   return SSSP_OK;
 }
 
@@ -384,13 +385,13 @@ sssp_status validate_host(uint32_t n, uint64_t m, const uint64_t* ro, const uint
 void free_graph(sssp_graph* g) {
   if (!g) return;
   if (g->ws) workspace_free(g->ws);
-  cudaFree(g->row_off);
-  cudaFree(g->edges);
-  cudaFree(g->out_min);
-  cudaFree(g->in_min);
-  cudaFree(g->rowdeg);
-  cudaFree(g->rrow_off);
-  cudaFree(g->redges);
+  dev_free(g->row_off);
+  dev_free(g->edges);
+  dev_free(g->out_min);
+  dev_free(g->in_min);
+  dev_free(g->rowdeg);
+  dev_free(g->rrow_off);
+  dev_free(g->redges);
   delete g;
 }
 
@@ -399,53 +400,51 @@ sssp_status build(sssp_graph* g, const uint64_t* ro_in, const uint32_t* col_in, 
   const uint32_t n = g->n;
   const uint64_t m = g->m;
   const cudaMemcpyKind kind = on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  SSSP_CUDA_TRY(cudaMalloc(&g->row_off, (n + 1ull) * sizeof(uint64_t)));
-  SSSP_CUDA_TRY(cudaMalloc(&g->edges, std::max<uint64_t>(m, 1) * sizeof(uint2)));
-  SSSP_CUDA_TRY(cudaMalloc(&g->out_min, n * sizeof(uint32_t)));
-  SSSP_CUDA_TRY(cudaMalloc(&g->in_min, n * sizeof(uint32_t)));
-  SSSP_CUDA_TRY(cudaMalloc(&g->rowdeg, n * sizeof(uint2)));
+  sssp_status s = SSSP_OK;
+  if ((s = dev_alloc(&g->row_off, n + 1ull)) != SSSP_OK || (s = dev_alloc(&g->edges, m)) != SSSP_OK ||
+      (s = dev_alloc(&g->out_min, n)) != SSSP_OK || (s = dev_alloc(&g->in_min, n)) != SSSP_OK ||
+      (s = dev_alloc(&g->rowdeg, n)) != SSSP_OK)
+    return s;
   SSSP_CUDA_TRY(cudaMemcpyAsync(g->row_off, ro_in, (n + 1ull) * sizeof(uint64_t), kind, st));
   if (m > 0) {
-    uint32_t* tmp = nullptr;
-    SSSP_CUDA_TRY(cudaMallocAsync(&tmp, 2 * m * sizeof(uint32_t), st));
+    TmpBuf<uint32_t> tbuf(st);
+    if ((s = tbuf.alloc(2 * m)) != SSSP_OK) return s;
+    uint32_t* tmp = tbuf.p;
     SSSP_CUDA_TRY(cudaMemcpyAsync(tmp, col_in, m * sizeof(uint32_t), kind, st));
     SSSP_CUDA_TRY(cudaMemcpyAsync(tmp + m, w_in, m * sizeof(uint32_t), kind, st));
     if (on_dev) {
-      unsigned int* bad = nullptr;
+      TmpBuf<unsigned int> bbuf(st);
+      if ((s = bbuf.alloc(1)) != SSSP_OK) return s;
+      unsigned int* bad = bbuf.p;
       unsigned int hbad = 0;
-      SSSP_CUDA_TRY(cudaMallocAsync(&bad, sizeof(unsigned int), st));
       SSSP_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(unsigned int), st));
       k_validate<<<grid_for(m + n, 256), 256, 0, st>>>(g->row_off, tmp, tmp + m, n, m, bad);
       SSSP_CUDA_TRY(cudaMemcpyAsync(&hbad, bad, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
       SSSP_CUDA_TRY(cudaStreamSynchronize(st));
-      SSSP_CUDA_TRY(cudaFreeAsync(bad, st));
       if (hbad) {
-        cudaFreeAsync(tmp, st);
-        cudaStreamSynchronize(st);
         return fail(SSSP_ERR_INVALID_ARG, "device CSR is invalid (%s%s%s)", (hbad & 1) ? "offsets " : "",
                     (hbad & 2) ? "targets " : "", (hbad & 4) ? "costs" : "");
       }
     }
     k_interleave<<<grid_for(m, 256), 256, 0, st>>>(tmp, tmp + m, m, reinterpret_cast<unsigned long long*>(g->edges));
     SSSP_CUDA_TRY(cudaGetLastError());
-    SSSP_CUDA_TRY(cudaFreeAsync(tmp, st));
   } else if (on_dev) {
     uint64_t h[2] = {0, 0};
     SSSP_CUDA_TRY(cudaMemcpyAsync(h, ro_in, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
     SSSP_CUDA_TRY(cudaStreamSynchronize(st));
     if (h[0] != 0) return fail(SSSP_ERR_INVALID_ARG, "device CSR is invalid (offsets)");
   }
-  sssp_status s = sort_rows(g->row_off, n, m, reinterpret_cast<unsigned long long*>(g->edges), st);
+  s = sort_rows(g->row_off, n, m, reinterpret_cast<unsigned long long*>(g->edges), st);
   if (s != SSSP_OK) return s;
   k_out_min<<<grid_for(n, 256), 256, 0, st>>>(g->row_off, g->edges, n, g->out_min, g->rowdeg);
   k_fill_u32<<<grid_for(n, 256), 256, 0, st>>>(g->in_min, n, kInf32);
   if (m > 0) k_in_min<<<grid_for(m, 256), 256, 0, st>>>(g->edges, m, g->in_min);
   SSSP_CUDA_TRY(cudaGetLastError());
   if (g->flags & SSSP_GRAPH_REVERSE) {
-    SSSP_CUDA_TRY(cudaMalloc(&g->rrow_off, (n + 1ull) * sizeof(uint64_t)));
-    SSSP_CUDA_TRY(cudaMalloc(&g->redges, std::max<uint64_t>(m, 1) * sizeof(uint2)));
-    uint32_t* cnt = nullptr;
-    SSSP_CUDA_TRY(cudaMallocAsync(&cnt, n * sizeof(uint32_t), st));
+    if ((s = dev_alloc(&g->rrow_off, n + 1ull)) != SSSP_OK || (s = dev_alloc(&g->redges, m)) != SSSP_OK) return s;
+    TmpBuf<uint32_t> cbuf(st);
+    if ((s = cbuf.alloc(n)) != SSSP_OK) return s;
+    uint32_t* cnt = cbuf.p;
     SSSP_CUDA_TRY(cudaMemsetAsync(cnt, 0, n * sizeof(uint32_t), st));
     if (m > 0) k_in_degree<<<grid_for(m, 256), 256, 0, st>>>(g->edges, m, cnt);
     s = exclusive_scan(cnt, n, g->rrow_off, st);
@@ -455,7 +454,7 @@ sssp_status build(sssp_graph* g, const uint64_t* ro_in, const uint32_t* col_in, 
       k_reverse_scatter<<<grid_for(32ull * n, 256), 256, 0, st>>>(g->row_off, g->edges, n, g->rrow_off, cnt,
                                                                    g->redges);
     SSSP_CUDA_TRY(cudaGetLastError());
-    SSSP_CUDA_TRY(cudaFreeAsync(cnt, st));
+    cbuf.release();
     s = sort_rows(g->rrow_off, n, m, reinterpret_cast<unsigned long long*>(g->redges), st);
     if (s != SSSP_OK) return s;
   }

@@ -36,6 +36,40 @@ bool is_device_pointer(const void* p);
 // Number of SMs of the current device.
 int sm_count();
 
+// Device allocations of the library (devmem.cu): counted, and refused with
+// SSSP_ERR_OUT_OF_MEMORY beyond the cap of sssp_set_device_memory_limit.
+sssp_status dev_malloc(void** p, size_t bytes);
+sssp_status dev_malloc_async(void** p, size_t bytes, cudaStream_t st);
+void dev_free(void* p);
+void dev_free_async(void* p, cudaStream_t st);
+
+template <class T>
+sssp_status dev_alloc(T** p, size_t count) {
+  return dev_malloc(reinterpret_cast<void**>(p), (count > 0 ? count : 1) * sizeof(T));
+}
+
+template <class T>
+sssp_status dev_alloc_async(T** p, size_t count, cudaStream_t st) {
+  return dev_malloc_async(reinterpret_cast<void**>(p), (count > 0 ? count : 1) * sizeof(T), st);
+}
+
+// A stream-ordered temporary that is released when it goes out of scope, so
+// that every early return of a failing call frees it.
+template <class T>
+struct TmpBuf {
+  T* p = nullptr;
+  cudaStream_t st;
+  explicit TmpBuf(cudaStream_t s) : st(s) {}
+  TmpBuf(const TmpBuf&) = delete;
+  TmpBuf& operator=(const TmpBuf&) = delete;
+  sssp_status alloc(size_t count) { return dev_alloc_async(&p, count, st); }
+  void release() {
+    dev_free_async(p, st);
+    p = nullptr;
+  }
+  ~TmpBuf() { release(); }
+};
+
 }  // namespace sssp
 
 #define SSSP_CUDA_TRY(expr)                                                                  \

@@ -169,7 +169,10 @@ extern "C" sssp_status sssp_policy_load(const float* weights, size_t count) {
   SSSP_CUDA_TRY(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxDevices) return fail(SSSP_ERR_UNSUPPORTED, "device ordinal out of range");
   std::lock_guard<std::mutex> lock(g_policy_mu);
-  if (!g_policy[dev]) SSSP_CUDA_TRY(cudaMalloc(&g_policy[dev], kPolWeights * sizeof(float)));
+  if (!g_policy[dev]) {
+    sssp_status s = dev_alloc(&g_policy[dev], kPolWeights);
+    if (s != SSSP_OK) return s;
+  }
   SSSP_CUDA_TRY(cudaMemcpy(g_policy[dev], weights, kPolWeights * sizeof(float),
                            is_device_pointer(weights) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
   return SSSP_OK;
@@ -180,7 +183,7 @@ extern "C" sssp_status sssp_policy_clear(void) {
   SSSP_CUDA_TRY(cudaGetDevice(&dev));
   std::lock_guard<std::mutex> lock(g_policy_mu);
   if (dev >= 0 && dev < kMaxDevices && g_policy[dev]) {
-    cudaFree(g_policy[dev]);
+    dev_free(g_policy[dev]);
     g_policy[dev] = nullptr;
   }
   return SSSP_OK;
@@ -210,13 +213,14 @@ extern "C" sssp_status sssp_mlp_backward(const float* w, const float* x, const f
   clear_error();
   if (!w || !x || !target || !arm || !grad || batch == 0) return fail(SSSP_ERR_INVALID_ARG, "NULL or empty argument");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  float* scr = nullptr;
-  SSSP_CUDA_TRY(cudaMallocAsync(&scr, (size_t)batch * kScr * sizeof(float), st));
+  TmpBuf<float> sbuf(st);
+  sssp_status s = sbuf.alloc((size_t)batch * kScr);
+  if (s != SSSP_OK) return s;
+  float* scr = sbuf.p;
   const int blocks = (int)std::min<uint32_t>((batch + 127) / 128, 1024);
   k_mlp_samples<<<blocks, 128, 0, st>>>(w, x, target, arm, batch, scr);
   k_mlp_grad_reduce<<<76, 256, 0, st>>>(x, scr, batch, grad, loss);
   SSSP_CUDA_TRY(cudaGetLastError());
-  SSSP_CUDA_TRY(cudaFreeAsync(scr, st));
   return SSSP_OK;
 }
 

@@ -103,3 +103,57 @@ def test_policy_features_follow_the_documented_formula():
         assert np.allclose(got, want, rtol=1e-5, atol=1e-6), (got, want)
     with pytest.raises(sp.SsspError):
         sp.policy_features(1, 0, 0, 1, 0, 0, 0)  # n = 0 is rejected
+
+
+def test_noalloc_rejects_misaligned_buffers_before_any_cuda_call():
+    """sssp_solve_noalloc reads its CSR and distance buffers as 8-byte words:
+    a buffer off an 8-byte boundary is refused with SSSP_ERR_INVALID_ARG by a
+    host-side check that runs before any CUDA call (so this needs no GPU)."""
+    import ctypes
+
+    import paper_1903_12085_gb300 as sp
+
+    L = sp.lib()
+    p = ctypes.c_void_p
+    for ro, ed, out in [(0x10004, 0x20000, 0x30000), (0x10000, 0x20004, 0x30000), (0x10000, 0x20000, 0x30002)]:
+        st = L.sssp_solve_noalloc(16, 8, p(ro), p(ed), 0, sp.IN_OUT, p(out), None, None)
+        assert st == 1
+        assert b"8-byte aligned" in L.sssp_last_error()
+
+
+def test_noalloc_binding_checks_its_tensors():
+    """The binding refuses CSR inputs the C ABI cannot check: host arrays,
+    wrong element sizes, strided views, too few offsets, an odd word count."""
+    import numpy as np
+    import torch
+
+    import paper_1903_12085_gb300 as sp
+
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        sp._noalloc_inputs(4, np.zeros(5, np.int64), np.zeros(2, np.int32))
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        sp._noalloc_inputs(4, torch.zeros(5, dtype=torch.int64), torch.zeros(2, dtype=torch.int32))
+
+
+def test_device_memory_cap_refuses_before_cudamalloc():
+    """With a cap below the first allocation, sssp_graph_create fails with
+    SSSP_ERR_OUT_OF_MEMORY before calling cudaMalloc (so this runs without a
+    GPU) and leaves nothing allocated; lifting the cap restores the default."""
+    import numpy as np
+
+    import paper_1903_12085_gb300 as sp
+
+    import ctypes
+
+    base = sp.device_memory_in_use()
+    sp.set_device_memory_limit(base + 1)
+    try:
+        ro, col, w = np.array([0, 1, 2, 2], np.uint64), np.array([1, 2], np.uint32), np.array([5, 6], np.uint32)
+        h = ctypes.c_void_p()
+        st = sp.lib().sssp_graph_create(3, 2, sp._ptr(ro), sp._ptr(col), sp._ptr(w), 0, sp.GRAPH_REVERSE, None,
+                                        ctypes.byref(h))
+        assert st == 2 and b"limit" in sp.lib().sssp_last_error()
+        assert h.value is None
+        assert sp.device_memory_in_use() == base
+    finally:
+        sp.set_device_memory_limit(0)
