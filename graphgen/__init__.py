@@ -183,7 +183,7 @@ WORKLOADS = {
     1: "gnm_n16384_m131072: directed G(n,m), n=16384, m=131072, w in [0,2^24), source 0",
     2: "grid_1024x1024: undirected 4-grid, w in [1,2^16), source (0,0)",
     3: "rmat_s22_ef16: R-MAT (.57,.19,.19,.05), w in [0,2^24), source = max out-degree",
-    4: "batch_256: 256 G(n,m), n in [2^10,2^18) octave-uniform, deg U[4,32], w in [0,2^20), 4 sources each",
+    4: "batch_256: 256 G(n,m), n log-uniform in [2^10,2^18), average degree U[4,32], w in [0,2^20), 4 sources each",
     5: "gnm_n2^24_m2^28: directed G(n,m), w in [0,2^24), 8 uniform sources",
 }
 
@@ -192,7 +192,7 @@ def workload(k: int, shrink: int = 0) -> Workload:
     """Workload k (1..5).  ``shrink`` > 0 gives a smaller graph of the same
     family for fast tests: every size parameter is divided by 2^shrink (grid
     sides by 2^(shrink/2) each, R-MAT scale reduced by shrink, the batch keeps
-    at most 256 >> shrink graphs with octaves shifted down)."""
+    at most 256 >> shrink graphs with the n range shifted down)."""
     seed = SEED_BASE + k
     if k == 1:
         n, m = 16384 >> shrink, 131072 >> shrink

@@ -168,23 +168,55 @@ int gg_rmat(uint32_t scale, uint64_t m, uint32_t ta, uint32_t tab, uint32_t tabc
     return rc;
 }
 
+/* Fractional part of log2(x) for x in [2^L, 2^(L+1)), in Q32 (0 .. 2^32-1),
+ * by the bit-by-bit squaring method: with y = x / 2^L in [1, 2) held in Q31,
+ * each step squares y; a square >= 2 yields a 1 bit and is halved.  Integer
+ * arithmetic with truncation only, so every host computes the same bits, and
+ * the result never decreases as x grows. */
+static uint32_t gg_log2_frac_q32(uint32_t x, uint32_t L) {
+    uint64_t y = (uint64_t)x << (31 - L);  /* in [2^31, 2^32) */
+    uint32_t f = 0;
+    for (int i = 0; i < 32; ++i) {
+        y = (y * y) >> 31;
+        f <<= 1;
+        if (y >= (1ull << 32)) { y >>= 1; f |= 1u; }
+    }
+    return f;
+}
+
+/* floor(2^t) for t = T / 2^32 (Q32, integer part 0..30): the largest x in
+ * [2^L, 2^(L+1)) whose log2 fraction does not exceed that of t. */
+static uint32_t gg_exp2_floor(uint64_t T) {
+    const uint32_t L = (uint32_t)(T >> 32), f = (uint32_t)T;
+    uint32_t lo = 1u << L, hi = (L < 31) ? (1u << (L + 1)) - 1 : 0xFFFFFFFFu;
+    while (lo < hi) {  /* invariant: the answer lies in [lo, hi] */
+        uint32_t mid = lo + (hi - lo + 1) / 2;
+        if (gg_log2_frac_q32(mid, L) <= f) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
 /* Parameters of the uneven batch: for graph g the caller receives n_g, m_g, its
- * seed and `sources_per_graph` source vertices.  n is drawn octave-uniform in
- * [2^lo_exp, 2^hi_exp): an octave L uniform in [lo_exp, hi_exp), then n uniform
- * in [2^L, 2^(L+1)) -- a piecewise-uniform stand-in for log-uniform that needs
- * no floating point.  The average out-degree is uniform on the 1/16 grid of
- * [deg_lo, deg_hi] and m = round(n * deg). */
+ * seed and `sources_per_graph` source vertices.  n is log-uniform in
+ * [2^lo_exp, 2^hi_exp): one 32-bit draw u gives t = lo_exp + (hi_exp - lo_exp)
+ * * u / 2^32 in Q32 and n = floor(2^t) (integer fixed-point, above).  The
+ * average out-degree is uniform in [deg_lo, deg_hi] (deg = deg_lo + (deg_hi -
+ * deg_lo) * u' / 2^32 for a second draw u') and m = round(n * deg). */
 int gg_batch_params(uint32_t count, uint32_t lo_exp, uint32_t hi_exp, uint32_t deg_lo,
                     uint32_t deg_hi, uint32_t sources_per_graph, uint64_t seed,
                     uint32_t* n_out, uint64_t* m_out, uint64_t* seed_out, uint32_t* src_out) {
-    if (hi_exp <= lo_exp || hi_exp > 31 || deg_hi < deg_lo) return -1;
+    if (hi_exp <= lo_exp || hi_exp > 30 || deg_hi < deg_lo || deg_hi > 1024) return -1;
     gg_rng r = {seed};
     for (uint32_t g = 0; g < count; ++g) {
-        uint32_t L = lo_exp + gg_bounded(gg_next(&r), hi_exp - lo_exp);
-        uint32_t n = (1u << L) + gg_bounded(gg_next(&r), 1ull << L);
-        uint64_t d16 = 16ull * deg_lo + gg_bounded(gg_next(&r), 16ull * (deg_hi - deg_lo) + 1);
+        const uint64_t u = gg_next(&r) >> 32;
+        const uint64_t T = ((uint64_t)lo_exp << 32) + (uint64_t)(hi_exp - lo_exp) * u;
+        const uint32_t n = gg_exp2_floor(T);
+        const uint64_t v = gg_next(&r) >> 32;
+        /* n * deg * 2^32 = n * (deg_lo * 2^32 + (deg_hi - deg_lo) * v) < 2^30 * 2^43 */
+        const uint64_t deg_q32 = ((uint64_t)deg_lo << 32) + (uint64_t)(deg_hi - deg_lo) * v;
+        const unsigned __int128 prod = (unsigned __int128)n * deg_q32;
         n_out[g] = n;
-        m_out[g] = ((uint64_t)n * d16 + 8) / 16;
+        m_out[g] = (uint64_t)((prod + (1ull << 31)) >> 32);
         seed_out[g] = seed + ((uint64_t)(g + 1) << 20);
         for (uint32_t k = 0; k < sources_per_graph; ++k)
             src_out[(size_t)g * sources_per_graph + k] = gg_bounded(gg_next(&r), n);
