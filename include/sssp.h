@@ -214,13 +214,27 @@ sssp_status sssp_solve_batch(sssp_graph* const* graphs, const uint32_t* sources,
 /* A prepared batch: descriptors and workspaces allocated once, the launch
  * captured in a CUDA graph.  sssp_batch_launch replays it on `stream`
  * (stream-ordered, returns immediately); outputs are the device buffers given
- * at creation.  phases_out must be device memory here. */
+ * at creation.  phases_out must be device memory here.  With
+ * SSSP_POLICY_LEARNED the batch copies the policy network loaded at creation
+ * and uses that copy in every launch (loading or clearing a network later does
+ * not affect it); its graphs need SSSP_GRAPH_REVERSE for the IN-SIMPLE arms. */
 typedef struct sssp_batch sssp_batch;
 sssp_status sssp_batch_create(sssp_graph* const* graphs, const uint32_t* sources, uint32_t count,
                               uint32_t criterion, uint64_t* const* dist_out, uint64_t* phases_out,
                               void* stream, sssp_batch** out);
 sssp_status sssp_batch_launch(sssp_batch* b, void* stream);
 void sssp_batch_destroy(sssp_batch* b);
+
+/* Diagnostics for solve i (caller order) of a prepared batch: every later
+ * launch writes its per-phase records (trace_cap of them) to `trace` and the
+ * phase in which each vertex settled (0 = never) to `settle_phase`, both
+ * device memory owned by the caller (NULL stops that output).  The records are
+ * those of sssp_solve_trace; with SSSP_POLICY_LEARNED they give the arm each
+ * phase ran with, so the schedule of a batched solve can be replayed.  Call it
+ * when no launch of the batch is in flight; synchronous on `stream`.  A
+ * library feature with no counterpart in the paper. */
+sssp_status sssp_batch_trace(sssp_batch* b, uint32_t i, sssp_phase_record* trace, uint64_t trace_cap,
+                             uint32_t* settle_phase, void* stream);
 
 /* Autotuner of a prepared batch: picks the number of blocks per solve from
  * the ladder 1, 2, 4, ..., all co-resident blocks (plus the batch's own
@@ -238,7 +252,7 @@ sssp_status sssp_batch_autotune(sssp_batch* b, void* stream, uint32_t* bpg_out, 
 
 /* ---- per-phase policy network ------------------------------------------
  * With SSSP_POLICY_LEARNED (criterion bits must be IN_STATIC | OUT_STATIC, the
- * fallback arm) every phase picks one of four arms:
+ * fallback arm) every phase of a single or batched solve picks one of four arms:
  *   0: IN-STATIC | OUT-STATIC, sparse queue   1: the same, dense scan
  *   2: IN-SIMPLE | OUT-STATIC, sparse queue   3: the same, dense scan
  * with a small MLP over 8 phase-start features (IN-SIMPLE arms need a graph

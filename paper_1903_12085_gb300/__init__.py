@@ -89,6 +89,7 @@ def lib():
             "sssp_solve_batch": [p, p, u32, u32, p, p, p],
             "sssp_batch_create": [p, p, u32, u32, p, p, p, ctypes.POINTER(p)],
             "sssp_batch_launch": [p, p],
+            "sssp_batch_trace": [p, u32, p, u64, p, p],
             "sssp_set_wait_limit_ns": [u64],
             "sssp_set_device_memory_limit": [u64],
             "sssp_device_memory_in_use": [p],
@@ -426,6 +427,31 @@ class Batch:
 
     def launch(self, stream=None):
         _check(lib().sssp_batch_launch(self.handle, _stream_ptr(stream)))
+
+    def attach_trace(self, i: int, trace_cap: int = 1 << 20, stream=None):
+        """sssp_batch_trace: later launches record solve i's per-phase records
+        (up to trace_cap) and per-vertex settle phases into device buffers
+        owned here; read them with ``trace_of(i)``."""
+        torch = _torch()
+        tr = torch.zeros(trace_cap * PHASE_RECORD.itemsize, dtype=torch.uint8, device="cuda")
+        settle = torch.zeros(self.graphs[i].n, dtype=torch.int32, device="cuda")
+        _check(lib().sssp_batch_trace(self.handle, int(i), _ptr(tr), int(trace_cap), _ptr(settle),
+                                      _stream_ptr(stream)))
+        if not hasattr(self, "_traces"):
+            self._traces = {}
+        self._traces[i] = (tr, settle, trace_cap)
+
+    def detach_trace(self, i: int, stream=None):
+        """sssp_batch_trace with no buffers: later launches stop recording
+        solve i (its last records stay readable with ``trace_of``)."""
+        _check(lib().sssp_batch_trace(self.handle, int(i), None, 0, None, _stream_ptr(stream)))
+
+    def trace_of(self, i: int):
+        """(settle_phase numpy uint32, trace records) of solve i after a launch."""
+        tr, settle, cap = self._traces[i]
+        phases = int(self.phases[i].item())
+        recs = tr.cpu().numpy().view(PHASE_RECORD)[:min(cap, phases)]
+        return settle.cpu().numpy().view(np.uint32), recs
 
     def autotune(self, stream=None):
         """sssp_batch_autotune: walk the blocks-per-solve ladder from the

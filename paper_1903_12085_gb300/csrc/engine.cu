@@ -1646,7 +1646,7 @@ __global__ void __launch_bounds__(kThreads) k_solve_batch(const BatchItem* items
                                                            unsigned int* next, GroupSlot* groups, uint32_t bpg,
                                                            uint32_t crit, BatchTuning tu,
                                                            unsigned long long wait_ns, int* err,
-                                                           unsigned long long* phases_out) {
+                                                           unsigned long long* phases_out, const float* policy) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned int s_item;
   const unsigned int gidx = blockIdx.x / bpg, rank = blockIdx.x % bpg;
@@ -1671,7 +1671,7 @@ __global__ void __launch_bounds__(kThreads) k_solve_batch(const BatchItem* items
     p.nf_min = tu.nf_min;
     p.nf_target = tu.nf_target;
     p.nf_share = tu.nf_share;
-    p.policy = nullptr;
+    p.policy = policy;
     solve_body(p, grp, smem);
     if (*(volatile int*)err != 0) return;
     if (rank == 0 && threadIdx.x == 0) {
@@ -1924,8 +1924,10 @@ struct BatchPlan {
   GroupSlot* gslots = nullptr;         // device, one per group
   int* err = nullptr;                  // device
   std::vector<Workspace*> ws;          // one per solve
+  std::vector<BatchItem> h_items;      // host copy of the descriptors (same order)
   unsigned long long* phases = nullptr;  // device [count], caller order
   bool own_phases = false;
+  float* policy = nullptr;             // device copy of the policy network taken at creation
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
 };
@@ -1946,6 +1948,7 @@ void batch_free(sssp_batch* b) {
   dev_free(b->next);
   dev_free(b->gslots);
   dev_free(b->err);
+  dev_free(b->policy);
   if (b->own_phases) dev_free(b->phases);
   delete b;
 }
@@ -1960,7 +1963,8 @@ sssp_status batch_enqueue(sssp_batch* b, cudaStream_t st) {
   const int blocks = (int)(b->groups * b->bpg);
   BatchTuning tu{solo_max(), solo_edges(), nearfar_min(), nearfar_target(), nearfar_share()};
   unsigned long long wait = wait_limit_ns();
-  void* args[] = {&b->items, &b->count, &b->next, &b->gslots, &b->bpg, &b->crit, &tu, &wait, &b->err, &b->phases};
+  void* args[] = {&b->items, &b->count, &b->next, &b->gslots, &b->bpg, &b->crit, &tu, &wait, &b->err, &b->phases,
+                  &b->policy};
   SSSP_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_solve_batch, dim3(blocks), dim3(kThreads), args,
                                             kSmemBytes, st));
   return SSSP_OK;
@@ -1970,7 +1974,6 @@ sssp_status batch_build(sssp_graph* const* graphs, const uint32_t* sources, uint
                         uint64_t* const* dist_out, uint64_t* phases_dev, uint32_t bpg, cudaStream_t st,
                         sssp_batch** out) {
   if (!graphs || !sources || !dist_out || count == 0) return fail(SSSP_ERR_INVALID_ARG, "empty or NULL batch");
-  if (crit & SSSP_POLICY_LEARNED) return fail(SSSP_ERR_UNSUPPORTED, "batches run without the phase policy");
   for (uint32_t i = 0; i < count; ++i) {
     if (!graphs[i]) return fail(SSSP_ERR_INVALID_ARG, "graph %u is NULL", i);
     if (sources[i] >= graphs[i]->n) return fail(SSSP_ERR_INVALID_ARG, "source of solve %u out of range", i);
@@ -1999,7 +2002,7 @@ sssp_status batch_build(sssp_graph* const* graphs, const uint32_t* sources, uint
   });
   std::vector<BatchItem> h(count);
   b->ws.assign(count, nullptr);
-  const bool cursors = (crit & (SSSP_IN_SIMPLE | SSSP_OUT_SIMPLE | SSSP_IN_FULL | SSSP_APPROX)) != 0;
+  const bool cursors = (crit & (SSSP_IN_SIMPLE | SSSP_OUT_SIMPLE | SSSP_IN_FULL | SSSP_APPROX | SSSP_POLICY_LEARNED)) != 0;
   for (uint32_t k = 0; k < count; ++k) {
     const uint32_t i = order[k];
     if ((s = workspace_alloc(graphs[i]->n, graphs[i]->m, cursors, false, &b->ws[k])) != SSSP_OK) {
@@ -2026,11 +2029,23 @@ sssp_status batch_build(sssp_graph* const* graphs, const uint32_t* sources, uint
       return s;
     }
   }
+  if (crit & SSSP_POLICY_LEARNED) {  // the batch keeps the network loaded now, whatever is loaded later
+    if ((s = dev_alloc(&b->policy, kPolWeights)) != SSSP_OK) {
+      batch_free(b);
+      return s;
+    }
+    if (cudaMemcpyAsync(b->policy, policy_weights(), kPolWeights * sizeof(float), cudaMemcpyDeviceToDevice, st) !=
+        cudaSuccess) {
+      batch_free(b);
+      return fail(SSSP_ERR_CUDA, "copy of the policy network failed");
+    }
+  }
   if (cudaMemcpyAsync(b->items, h.data(), count * sizeof(BatchItem), cudaMemcpyHostToDevice, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess) {
     batch_free(b);
     return fail(SSSP_ERR_CUDA, "copy of batch descriptors failed");
   }
+  b->h_items = std::move(h);
   *out = b;
   return SSSP_OK;
 }
@@ -2222,6 +2237,26 @@ extern "C" sssp_status sssp_batch_autotune(sssp_batch* b, void* stream, uint32_t
   if (sc != SSSP_OK) return sc;
   if (bpg_out) *bpg_out = best;
   if (ms_out) *ms_out = best_ms;
+  return SSSP_OK;
+}
+
+extern "C" sssp_status sssp_batch_trace(sssp_batch* b, uint32_t i, sssp_phase_record* trace, uint64_t trace_cap,
+                                        uint32_t* settle_phase, void* stream) {
+  clear_error();
+  if (!b) return fail(SSSP_ERR_INVALID_ARG, "batch is NULL");
+  if (i >= b->count) return fail(SSSP_ERR_INVALID_ARG, "solve %u out of range (batch of %u)", i, b->count);
+  if ((trace && trace_cap && !is_device_pointer(trace)) || (settle_phase && !is_device_pointer(settle_phase)))
+    return fail(SSSP_ERR_INVALID_ARG, "trace and settle_phase of a batched solve must be device memory");
+  uint32_t k = 0;
+  while (k < b->count && b->h_items[k].out_index != i) ++k;
+  if (k == b->count) return fail(SSSP_ERR_INTERNAL, "solve %u has no descriptor", i);
+  BatchItem& it = b->h_items[k];
+  it.ws.trace = trace_cap ? trace : nullptr;
+  it.ws.trace_cap = trace ? trace_cap : 0;
+  it.ws.settle_phase = settle_phase;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  SSSP_CUDA_TRY(cudaMemcpyAsync(&b->items[k], &it, sizeof(BatchItem), cudaMemcpyHostToDevice, st));
+  SSSP_CUDA_TRY(cudaStreamSynchronize(st));
   return SSSP_OK;
 }
 

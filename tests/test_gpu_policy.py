@@ -107,6 +107,55 @@ def test_policy_solves_are_exact_and_replayable(tune):
         sp.set_tuning()
 
 
+@pytest.mark.parametrize("bpg", [1, 3], ids=["bpg1", "bpg3"])
+def test_batched_policy_solves_are_exact_and_replayable(bpg):
+    """The learned policy inside one batched persistent launch: graphs of
+    three families with two sources each, a random network switching arms
+    phase by phase in every group.  Every solve's distances equal Dijkstra's;
+    for traced solves the simulator, fed the logged per-phase criteria,
+    settles the same vertices in every phase (soundness of switching: any
+    disjunction of sound criteria is sound, Section 3)."""
+    sp.set_tuning(batch_blocks_per_solve=bpg)
+    try:
+        sp.policy_load(omlp.init(211, scale=1.0).astype(np.float32))
+        wls = [gg.workload(1, shrink=2), gg.workload(3, shrink=12), gg.workload(2, shrink=10),
+               gg.workload(5, shrink=11)]
+        graphs, Gs, srcs = [], [], []
+        for wl in wls:
+            g = wl.graphs[0]
+            G = sp.Graph.from_csr(g, reverse=True)
+            for j in range(2):
+                s = wl.solves[0][1] if j == 0 else (wl.solves[0][1] + g.n // 3) % g.n
+                graphs.append(g)
+                Gs.append(G)
+                srcs.append(s)
+        B = sp.Batch(Gs, srcs, sp.IN_OUT | sp.POLICY_LEARNED)
+        sp.policy_clear()  # the batch keeps its own copy of the network
+        traced = list(range(0, len(Gs), 2))
+        for i in traced:
+            B.attach_trace(i)
+        for rep in range(2):  # a replay of the captured launch gives the same results
+            B.launch()
+            torch.cuda.synchronize()
+            phases = B.phases.cpu().numpy()
+            for i, (g, s) in enumerate(zip(graphs, srcs)):
+                ref = oracle.dijkstra(g, s)
+                assert (sp.as_uint64(B.outs[i]) == ref).all(), f"solve {i}"
+                if i in traced:
+                    settle, tr = B.trace_of(i)
+                    assert len(tr) == phases[i]
+                    sched = tr["criterion"].astype(np.uint32)
+                    assert set(np.unique(sched)) <= {sp.IN_OUT, sp.IN_SIMPLE | sp.OUT_STATIC}
+                    assert ((tr["arm"] & 0x80) != 0).all()
+                    sim = oracle.simulate(g, s, sp.IN_OUT, schedule=sched, dist_ref=ref)
+                    assert sim.phases == phases[i]
+                    assert (settle == sim.settle_phase).all(), f"solve {i}"
+        B.close()
+    finally:
+        sp.policy_clear()
+        sp.set_tuning()
+
+
 def test_policy_requires_a_loaded_network_and_the_fallback_criterion():
     g = gg.workload(1, shrink=4).graphs[0]
     G = sp.Graph.from_csr(g, reverse=True)
