@@ -6,6 +6,8 @@ imports, links or runs anything here, and this package shares no code with it.
 
 * ``dijkstra``      binary-heap Dijkstra (Section 2): the plain definition of
                     dist(s, v), UINT64_MAX for unreachable vertices.
+* ``dijkstra_prefix``  the same run stopped after a number of settled vertices
+                    (a bounded sample of a solve's work, for the CPU timings).
 * ``bellman_ford``  brute-force relaxation of all edges, for small graphs.
 * ``simulate``      the generic phased algorithm (Section 3) with the IN/OUT
                     criteria of Section 3 (eqs. crit:in, crit:out, crit:outweak,
@@ -68,6 +70,8 @@ def _configure(lib):
         f = getattr(lib, name)
         f.restype = ctypes.c_int
         f.argtypes = [u32, p, p, p, u32, p]
+    lib.orc_dijkstra_prefix.restype = ctypes.c_int
+    lib.orc_dijkstra_prefix.argtypes = [u32, p, p, p, u32, u64, p, p]
     lib.orc_simulate.restype = ctypes.c_int
     lib.orc_simulate.argtypes = [u32, p, p, p, u32, p, u64, u32, p, p, p, p, p, u64]
     return lib
@@ -98,6 +102,20 @@ def dijkstra(g, s: int) -> np.ndarray:
     if rc:
         raise RuntimeError(f"orc_dijkstra: {_ERRORS.get(rc, rc)}")
     return dist
+
+
+def dijkstra_prefix(g, s: int, max_settled: int):
+    """Dijkstra from s stopped after max_settled settled vertices (a bounded
+    sample of a solve, for timing).  Returns (settled, sum of their
+    out-degrees)."""
+    ro, col, w = _csr(g)
+    dist = np.empty(g.n, np.uint64)
+    counts = np.zeros(2, np.uint64)
+    rc = _load().orc_dijkstra_prefix(g.n, ro.ctypes.data, col.ctypes.data, w.ctypes.data, s, int(max_settled),
+                                     dist.ctypes.data, counts.ctypes.data)
+    if rc:
+        raise RuntimeError(f"orc_dijkstra_prefix: {_ERRORS.get(rc, rc)}")
+    return int(counts[0]), int(counts[1])
 
 
 def bellman_ford(g, s: int) -> np.ndarray:

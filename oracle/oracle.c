@@ -10,6 +10,8 @@
  * Contents
  *   orc_dijkstra      Dijkstra's algorithm (Section 2) with a binary heap and
  *                     lazy deletion: the plain definition of dist(s, v).
+ *   orc_dijkstra_prefix  the same run stopped after a given number of settled
+ *                     vertices (a bounded sample of its work, for timing).
  *   orc_bellman_ford  n-1 rounds of relaxing every edge: an independent
  *                     brute-force check of the distances on small graphs.
  *   orc_simulate      the generic phased SSSP algorithm (Section 3) run with a
@@ -110,10 +112,12 @@ static orc_item heap_pop(orc_heap* h) {
 }
 
 /* Dijkstra (Section 2): repeatedly settle the fringe vertex of minimum
- * tentative distance and relax its out-edges.  Returns 0, -1 on OOM, -2 on a
- * bad argument. */
-int orc_dijkstra(uint32_t n, const uint64_t* row_off, const uint32_t* col, const uint32_t* w,
-                 uint32_t s, uint64_t* dist) {
+ * tentative distance and relax its out-edges, until the heap is empty or
+ * max_settled vertices are settled.  counts (may be NULL) receives the number
+ * of settled vertices and the sum of their out-degrees.  Returns 0, -1 on OOM,
+ * -2 on a bad argument. */
+static int dijkstra_run(uint32_t n, const uint64_t* row_off, const uint32_t* col, const uint32_t* w,
+                        uint32_t s, uint64_t max_settled, uint64_t* dist, uint64_t* counts) {
     if (s >= n) return -2;
     for (uint32_t v = 0; v < n; ++v) dist[v] = ORC_INF64;
     uint8_t* done = (uint8_t*)calloc(n, 1);
@@ -121,11 +125,14 @@ int orc_dijkstra(uint32_t n, const uint64_t* row_off, const uint32_t* col, const
     if (!done) return -1;
     dist[s] = 0;
     if (heap_push(&h, 0, s)) { free(done); return -1; }
-    while (h.len) {
+    uint64_t settled = 0, scanned = 0;
+    while (h.len && settled < max_settled) {
         orc_item it = heap_pop(&h);
         uint32_t u = it.v;
         if (done[u] || it.key != dist[u]) continue;
         done[u] = 1;
+        ++settled;
+        scanned += row_off[u + 1] - row_off[u];
         for (uint64_t e = row_off[u]; e < row_off[u + 1]; ++e) {
             uint32_t t = col[e];
             uint64_t cand = dist[u] + w[e];
@@ -137,7 +144,20 @@ int orc_dijkstra(uint32_t n, const uint64_t* row_off, const uint32_t* col, const
     }
     free(h.a);
     free(done);
+    if (counts) { counts[0] = settled; counts[1] = scanned; }
     return 0;
+}
+
+int orc_dijkstra(uint32_t n, const uint64_t* row_off, const uint32_t* col, const uint32_t* w,
+                 uint32_t s, uint64_t* dist) {
+    return dijkstra_run(n, row_off, col, w, s, UINT64_MAX, dist, NULL);
+}
+
+/* The first max_settled settled vertices of a Dijkstra run (a bounded sample
+ * of a solve's work for timing; dist is final only for the settled ones). */
+int orc_dijkstra_prefix(uint32_t n, const uint64_t* row_off, const uint32_t* col, const uint32_t* w,
+                        uint32_t s, uint64_t max_settled, uint64_t* dist, uint64_t* counts) {
+    return dijkstra_run(n, row_off, col, w, s, max_settled, dist, counts);
 }
 
 /* Bellman-Ford: relax every edge until nothing changes (at most n-1 rounds). */

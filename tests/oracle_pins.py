@@ -324,7 +324,33 @@ def pin_approx_sound_between(O, cases=80, seed=21):
                 assert thr[0] <= thr[1] <= thr[2], (p, thr)
 
 
+def pin_dijkstra_prefix(O, cases=300, seed=22):
+    """A Dijkstra run stopped after k settled vertices has settled the k
+    reachable vertices of least distance (distances from Bellman-Ford, the
+    reachable set from BFS): its settled count is min(k, reachable) and its
+    scanned-edge count is the sum of their out-degrees (graphs whose k-th and
+    (k+1)-th distances tie are skipped: either vertex may come first)."""
+    rng = np.random.default_rng(seed)
+    checked = 0
+    for _ in range(cases):
+        g = random_tiny_graph(rng, n_max=14, w_max=1000)
+        s = int(rng.integers(0, g.n))
+        bf = O.bellman_ford(g, s)
+        reach = bfs_reachable(g, s)
+        deg = np.diff(g.row_off.astype(np.int64))
+        order = sorted(np.flatnonzero(reach), key=lambda v: int(bf[v]))
+        for k in range(0, g.n + 2):
+            settled, scanned = O.dijkstra_prefix(g, s, k)
+            kk = min(k, len(order))
+            assert settled == kk, (k, settled, kk)
+            if 0 < kk < len(order) and bf[order[kk - 1]] == bf[order[kk]]:
+                continue
+            assert scanned == int(deg[order[:kk]].sum()), (k, scanned)
+            checked += 1
+    assert checked > 1000
+
+
 ALL_PINS = [pin_golden_examples, pin_bellman_ford_fuzz, pin_path_enumeration, pin_unit_grid,
             pin_path_graph, pin_out_star, pin_oracle_hops, pin_distance_invariants,
             pin_soundness_fuzz, pin_strength_chain, pin_trace_accounting,
-            pin_approx_k1_is_full_weak, pin_approx_sound_between]
+            pin_approx_k1_is_full_weak, pin_approx_sound_between, pin_dijkstra_prefix]
