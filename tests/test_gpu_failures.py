@@ -32,7 +32,8 @@ def _caps(base, need, points=48):
     evenly spread, so that every allocation of the call is refused by some of
     them."""
     caps = sorted({base + (need * i) // points for i in range(points)} | {base + need - 1})
-    return [c for c in caps if base <= c < base + need]
+    # a cap of 0 means "no cap": with nothing held yet, 1 byte stands for it
+    return [max(c, 1) for c in caps if base <= c < base + need]
 
 
 def _expect_oom(call, base):
@@ -136,7 +137,7 @@ def test_policy_load_out_of_memory():
     from oracle import mlp as omlp
     sp.policy_clear()
     base = sp.device_memory_in_use()
-    sp.set_device_memory_limit(base)
+    sp.set_device_memory_limit(max(base, 1))  # (a cap of 0 means "no cap")
     try:
         _expect_oom(lambda: sp.policy_load(omlp.init(1).astype(np.float32)), base)
     finally:
