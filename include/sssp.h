@@ -164,8 +164,10 @@ typedef struct {
   uint32_t criterion;      /* criterion mask applied in this phase */
   uint32_t arm;            /* bit 0: dense frontier; bit 1: phase ran on one block;
                               bit 2: near/far split active; bit 3: far part refilled
-                              (or split made) at phase start; bit 7: policy choice,
-                              bits 8..15: its arm index */
+                              by a scan of all vertices (or split made) at phase
+                              start; bit 4: bound raised from the far-vertex bucket
+                              lists instead; bit 7: policy choice, bits 8..15: its
+                              arm index */
   uint64_t t_start_ns;     /* device %globaltimer at phase start */
   uint64_t t_end_ns;       /* device %globaltimer at phase end */
   uint32_t queued;         /* fringe vertices in the scanned queue (|F| minus the
@@ -348,10 +350,13 @@ sssp_status sssp_solve_noalloc(uint32_t n, uint64_t m, const uint64_t* row_offse
  * scans, and a far part of vertices that no phase can settle before a bound B
  * on d(v) - inmin(v) is raised (0 = never split);
  * nearfar_target: vertices the near part is sized to when B is set or raised
- * (0 = chosen from n and the settled count of the last phase);
+ * (0 = four times the settled count of the last phase, at least 8192; by
+ * sssp_solve_noalloc, which keeps no bucket lists, chosen from n and that
+ * count); far vertices are listed in buckets of d(v) - inmin(v), so raising B
+ * usually reads just the passed buckets' lists, and all n vertex records only
+ * when B passes the listed range;
  * nearfar_min_share: the split also needs a fringe of at least this many
- * 256ths of n (a refill scans all n vertex records, which pays off only for a
- * fringe that is a sizeable share of the graph; 0 = no such condition).
+ * 256ths of n (0 = no such condition).
  * Applies to launches made after the call; sssp_set_tuning(NULL) restores the
  * defaults (4096, 0, 0, 2048, 8192, 0, 32). */
 typedef struct {

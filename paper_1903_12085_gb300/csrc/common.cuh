@@ -30,6 +30,13 @@ constexpr uint64_t kFarBit = 0x4000000000000000ull;
 constexpr uint64_t kNoBound = 0x3FFFFFFFFFFFFFFFull;  // B when no vertex is far
 constexpr uint32_t kNearFarMaxVertices = 1u << 30;
 constexpr int kNfBins = 256;  // key histogram: 4 bins per octave
+// Far vertices are also listed by key bucket: bucket i >= 1 holds keys in
+// [O + i * 2^s, O + (i + 1) * 2^s) (O and s fixed by the last split or full
+// refill, which set the bound B = O + 2^s - 1).  The near part is every bucket
+// up to the cursor c (B = O + (c + 1) * 2^s - 1); buckets c+1 .. c+kNfRing have
+// lists in a ring of kNfRing slots, so raising B moves just the listed
+// vertices of the buckets it passes.
+constexpr uint32_t kNfRing = 64;
 
 // Vertex status: unexplored, fringe (queued), settled (Section 2's U, F, S).
 enum : uint8_t { kU = 0, kF = 1, kS = 2 };
@@ -114,6 +121,13 @@ struct Ctl {
   unsigned int far_count;
   unsigned int nf_tmp;
   unsigned int hist[2][kNfBins];
+  // far-vertex buckets (see kNfRing; the geometry itself is computed alike in
+  // every block): the lowest bucket with a far vertex that has no list entry
+  // (kInf32 if none: past the ring when it was last lowered, or its list was
+  // full), and the list fills
+  unsigned int nf_beyond;
+  unsigned int nf_moved;  // vertices a pull moved to the queue (summed before the far count drops)
+  unsigned int nf_cnt[kNfRing];
 };
 
 // Mutable per-solve buffers.
@@ -130,6 +144,8 @@ struct SolveWS {
   unsigned long long* apx_in;   // [n] APPROX: approximate IN (full) values, or nullptr
   unsigned long long* apx_out;  // [n] APPROX: approximate OUT-WEAK values
   uint32_t* fresh;              // [n] APPROX: vertices that entered F in the last relax step
+  uint32_t* nf_list;            // [kNfRing * nf_cap] far-vertex bucket lists, or nullptr (full refills only)
+  uint32_t nf_cap;              // entries per bucket list
   unsigned long long* dist;  // [n] output distances
   Ctl* ctl;
   uint32_t* settle_phase;  // [n] optional
@@ -318,27 +334,43 @@ __device__ __forceinline__ bool bounded_wait_change(const unsigned int* addr, un
   return true;
 }
 
-// Barrier over the `size` blocks of a group (all co-resident).  rank 0 adds
-// 2^31 - (size - 1), the others 1; each block then waits (bounded) until the
-// counter's top bit differs from the one it saw.  The arrival is an acq_rel
-// atomic after a fence, so every write of the block before the barrier is
-// visible to every block after it.  Returns false in every thread of the block
-// if the wait ran out or an error was recorded.  All threads must call it.
+// Group barriers this block has passed (shared memory; zeroed by
+// grid_sync_init at kernel entry).  Every block of a group passes the same
+// barriers, so the count tells each block what the counter's top bit will be
+// once everyone has arrived at the next one.
+static __shared__ unsigned int s_bar_gen;
+
+__device__ __forceinline__ void grid_sync_init() {
+  if (threadIdx.x == 0) s_bar_gen = 0;
+  __syncthreads();
+}
+
+// Barrier over the `size` blocks of a group (all co-resident), on a counter
+// that is zero when the kernel starts.  rank 0 adds 2^31 - (size - 1), the
+// others 1, so the top bit flips exactly when all have arrived: after the g-th
+// barrier it equals g & 1.  The arrival is a release reduction (no round trip
+// back to the block), so every write of the block before the barrier (ordered
+// by the block barrier in front of it) is visible to every block that has seen
+// the flip with an acquire load.  Each wait is bounded; returns false in every
+// thread of the block if it ran out or an error was recorded.  All threads must
+// call it.
 __device__ __forceinline__ bool grid_sync(GridBarrier* bar, unsigned int rank, unsigned int size,
                                           unsigned long long limit_ns, int* err) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     const unsigned int add = rank == 0 ? 0x80000000u - (size - 1) : 1u;
-    __threadfence();
-    const unsigned int old = atom_add_acq_rel_gpu(&bar->count, add);
+    const unsigned int want = (++s_bar_gen & 1u) << 31;
+    red_release_gpu_add(&bar->count, add);
     int ok = 1;
-    const unsigned long long t0 = globaltimer_ns();
+    unsigned long long t0 = 0;
     unsigned int spins = 0;
-    while (((ld_acquire_gpu(&bar->count) ^ old) & 0x80000000u) == 0) {
+    while ((ld_acquire_gpu(&bar->count) & 0x80000000u) != want) {
       if ((++spins & 15u) == 0) {
         if (*(volatile int*)err != 0) { ok = 0; break; }
-        if (globaltimer_ns() - t0 > limit_ns) {
+        const unsigned long long now = globaltimer_ns();
+        if (t0 == 0) t0 = now;
+        else if (now - t0 > limit_ns) {
           atomicCAS(err, 0, (int)SSSP_ERR_TIMEOUT);
           ok = 0;
           break;

@@ -173,9 +173,9 @@ __device__ __forceinline__ unsigned long long in_min_full(const GraphView& g, co
 struct Shared {
   unsigned long long* red;    // 64
   unsigned long long* bases;  // 2: output offsets reserved by the block
-  uint32_t* s_base;           // kTile
-  uint32_t* s_row;            // kTile
-  unsigned long long* s_d;    // kTile
+  uint32_t* s_base;           // kWarps * kTile (one relax tile per warp)
+  uint32_t* s_row;            // kWarps * kTile
+  unsigned long long* s_d;    // kWarps * kTile
   uint32_t* s_range;          // 2
   uint32_t* scan;             // 34
 };
@@ -185,9 +185,9 @@ __device__ __forceinline__ Shared carve(unsigned char* smem) {
   s.red = reinterpret_cast<unsigned long long*>(smem);
   s.bases = s.red + 64;
   s.s_d = s.bases + 2;
-  s.s_base = reinterpret_cast<uint32_t*>(s.s_d + kTile);
-  s.s_row = s.s_base + kTile;
-  s.s_range = s.s_row + kTile;
+  s.s_base = reinterpret_cast<uint32_t*>(s.s_d + kWarps * kTile);
+  s.s_row = s.s_base + kWarps * kTile;
+  s.s_range = s.s_row + kWarps * kTile;
   s.scan = s.s_range + 2;
   return s;
 }
@@ -285,7 +285,7 @@ __device__ Arm choose_arm(const SolveParams& p, uint64_t k, uint32_t nQ, uint32_
 
 // Trace arm bits of the near/far split: split active in the phase; the far
 // part was refilled (or the split made) at the start of the phase.
-constexpr uint32_t kArmNfActive = 4u, kArmNfRefill = 8u;
+constexpr uint32_t kArmNfActive = 4u, kArmNfRefill = 8u, kArmNfPull = 16u;
 
 __device__ __forceinline__ uint32_t arm_code(const Arm& a, bool solo) {
   return (a.dense ? 1u : 0u) | (solo ? 2u : 0u) | (a.index >= 0 ? ((uint32_t)a.index << 8) | 0x80u : 0u);
@@ -303,6 +303,89 @@ __device__ __forceinline__ void reset_slot(PhaseSlot* s) {
   s->fresh_count = 0;
 }
 
+// Near/far state every relaxation needs: the bound B and the far-vertex
+// buckets (see kNfRing).  Identical in every block of the group.
+constexpr uint32_t kNoBucket = 0xFFFFFFFFu;
+struct NfView {
+  unsigned long long bound;   // B (kNoBound: no far vertex)
+  unsigned long long origin;  // O
+  uint32_t shift;             // s
+  uint32_t cursor;            // c
+  uint32_t cap;               // entries per list
+  uint32_t* lists;            // [kNfRing * cap], or nullptr: no lists (full refills only)
+  unsigned int* cnt;          // [kNfRing] list fills
+  unsigned int* beyond;       // lowest bucket with an unlisted far vertex
+};
+
+// Bucket of a far vertex's stored word (key > B >= O).
+__device__ __forceinline__ uint32_t nf_bucket(const NfView& nv, unsigned long long word, uint32_t im) {
+  const unsigned long long d = word & ~kFarBit;
+  const unsigned long long key = (im == kInf32 || d <= im) ? 0ull : d - im;
+  const unsigned long long x = key > nv.origin ? (key - nv.origin) >> nv.shift : 0ull;
+  return x < 0xFFFFFF00ull ? (uint32_t)x : 0xFFFFFF00u;
+}
+
+// Warp-aggregated listing of far vertices: lane with b != kNoBucket lists v in
+// bucket b (lanes with the same ring slot share one atomicAdd).  A bucket past
+// the ring or a full list leaves v unlisted and lowers `beyond` to b, so the
+// bound never passes b without a full refill.  All 32 lanes call it.
+__device__ __forceinline__ void nf_list_append(const NfView& nv, uint32_t b, uint32_t v) {
+  const bool want = b != kNoBucket;
+  if (!__any_sync(0xFFFFFFFFu, want)) return;
+  const unsigned int lane = threadIdx.x & 31;
+  const bool listed = want && b <= nv.cursor + kNfRing;
+  uint32_t unl = (want && !listed) ? b : kInf32;
+  const uint32_t slot = listed ? (b & (kNfRing - 1)) : kInf32;
+  const unsigned int peers = __match_any_sync(0xFFFFFFFFu, slot);
+  if (listed) {
+    const int leader = __ffs(peers) - 1;
+    uint32_t base = 0;
+    if ((int)lane == leader) base = atomicAdd(&nv.cnt[slot], (unsigned int)__popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    const uint32_t pos = base + __popc(peers & ((1u << lane) - 1u));
+    if (pos < nv.cap) nv.lists[(uint64_t)slot * nv.cap + pos] = v;
+    else unl = b;
+  }
+  unl = __reduce_min_sync(0xFFFFFFFFu, unl);
+  if (lane == 0 && unl != kInf32) atomicMin(nv.beyond, unl);
+}
+
+// nf_list_append for N items per lane at once: the slot atomics of all items
+// are issued before any of their results is used (one round trip, not N).
+template <int N>
+__device__ __forceinline__ void nf_list_append_n(const NfView& nv, const uint32_t (&b)[N], const uint32_t (&v)[N]) {
+  bool any = false;
+#pragma unroll
+  for (int i = 0; i < N; ++i) any |= b[i] != kNoBucket;
+  if (!__any_sync(0xFFFFFFFFu, any)) return;
+  const unsigned int lane = threadIdx.x & 31, lt = (1u << lane) - 1u;
+  uint32_t slot[N], base[N], rank[N];
+  int lead[N];
+  uint32_t unl = kInf32;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    const bool want = b[i] != kNoBucket;
+    const bool listed = want && b[i] <= nv.cursor + kNfRing;
+    if (want && !listed) unl = min(unl, b[i]);
+    slot[i] = listed ? (b[i] & (kNfRing - 1)) : kInf32;
+    const unsigned int peers = __match_any_sync(0xFFFFFFFFu, slot[i]);
+    lead[i] = __ffs(peers) - 1;
+    rank[i] = __popc(peers & lt);
+    base[i] = 0;
+    if (listed && (int)lane == lead[i]) base[i] = atomicAdd(&nv.cnt[slot[i]], (unsigned int)__popc(peers));
+  }
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    const uint32_t pos = __shfl_sync(0xFFFFFFFFu, base[i], lead[i]) + rank[i];
+    if (slot[i] != kInf32) {
+      if (pos < nv.cap) nv.lists[(uint64_t)slot[i] * nv.cap + pos] = v[i];
+      else unl = min(unl, b[i]);
+    }
+  }
+  unl = __reduce_min_sync(0xFFFFFFFFu, unl);
+  if (lane == 0 && unl != kInf32) atomicMin(nv.beyond, unl);
+}
+
 // Relaxation of one edge (u -> t) with d[u] = du (step C, any mode): one
 // load of t's record gives d[t] and whether t is settled (kSettledBit); a
 // settled target is skipped.  Otherwise d[t] is lowered to du + c: a target
@@ -311,33 +394,42 @@ __device__ __forceinline__ void reset_slot(PhaseSlot* s) {
 // below the value read before the update contributes to the next phase's fused
 // thresholds: the final d[t] is always contributed by the relaxation that
 // wrote it, and every contribution is >= the final d[t].
-// Near/far split (bound < kNoBound): the candidate is stored with kFarBit when
-// its key du + c - inmin(t) exceeds the bound.  A new vertex that is far is
-// only counted (dfar); a far vertex whose stored word loses the bit is moved
-// to the near queue by the one relaxation whose atomicMin saw the bit go.
-// `fresh` asks the caller to append t to the next queue.  kNF = false is the
-// same code for a solve with no far vertex (B = kNoBound).
+// Near/far split (B < kNoBound): the candidate is stored with kFarBit when its
+// key du + c - inmin(t) exceeds B.  A new vertex that is far is counted (dfar)
+// and listed in its bucket (`app`); a far vertex lowered into another bucket is
+// listed again (older entries go stale and are skipped when their bucket is
+// pulled); a far vertex whose stored word loses the bit is moved to the near
+// queue by the one relaxation whose atomicMin saw the bit go.  `fresh` asks the
+// caller to append t to the next queue.  kNF = false is the same code for a
+// solve with no far vertex (B = kNoBound).
 template <bool kNF>
-__device__ __forceinline__ void relax_edge(const SolveParams& p, const Mode& md, uint32_t t, uint32_t cost,
-                                           unsigned long long du, unsigned long long bound,
-                                           unsigned long long& pd, unsigned long long& po, bool& fresh, int& dfar) {
+__device__ __forceinline__ void relax_edge_rec(const SolveParams& p, const Mode& md, uint32_t t, uint32_t cost,
+                                               unsigned long long du, const VRec& rt, const NfView& nv,
+                                               unsigned long long& pd, unsigned long long& po, bool& fresh,
+                                               int& dfar, uint32_t& app) {
   const SolveWS& w = p.ws;
-  const VRec rt = ldcg_vrec(&w.vrec[t]);
   if (rt.d & kSettledBit) return;
   const unsigned long long cand = du + cost;
   unsigned long long enc = cand;
-  if (kNF && cand > bound + rt.im) enc |= kFarBit;
+  if (kNF && cand > nv.bound + rt.im) enc |= kFarBit;
   if (enc < rt.d) {
     unsigned long long old = rt.d;
     if (rt.d == kUnexplored) {
       old = atomicMin(&w.vrec[t].d, enc);
       if (old == kUnexplored) {
         w.status[t] = kF;
-        if (kNF && (enc & kFarBit)) ++dfar;
-        else fresh = true;
+        if (kNF && (enc & kFarBit)) {
+          ++dfar;
+          if (nv.lists) app = nf_bucket(nv, enc, rt.im);
+        } else {
+          fresh = true;
+        }
       } else if (kNF && (old & kFarBit) && !(enc & kFarBit)) {
         fresh = true;  // old < kUnexplored: t was far and is near now
         --dfar;
+      } else if (kNF && (enc & kFarBit) && enc < old && nv.lists) {
+        const uint32_t b = nf_bucket(nv, enc, rt.im);  // lowered another relaxation's far value
+        if (b != nf_bucket(nv, old, rt.im)) app = b;
       }
     } else if (kNF && (rt.d & kFarBit) && !(enc & kFarBit)) {
       old = atomicMin(&w.vrec[t].d, enc);
@@ -347,6 +439,10 @@ __device__ __forceinline__ void relax_edge(const SolveParams& p, const Mode& md,
       }
     } else {
       red_min_u64(&w.vrec[t].d, enc);
+      if (kNF && (enc & kFarBit) && nv.lists) {  // far and lowered (rt.d is far: its key is larger)
+        const uint32_t b = nf_bucket(nv, enc, rt.im);
+        if (b != nf_bucket(nv, rt.d, rt.im)) app = b;
+      }
     }
     if (md.fused && enc < old) {
       pd = cand < pd ? cand : pd;
@@ -358,6 +454,15 @@ __device__ __forceinline__ void relax_edge(const SolveParams& p, const Mode& md,
   }
 }
 
+// The same with t's record loaded here (rt above is the record as read
+// before any update of this relaxation).
+template <bool kNF>
+__device__ __forceinline__ void relax_edge(const SolveParams& p, const Mode& md, uint32_t t, uint32_t cost,
+                                           unsigned long long du, const NfView& nv, unsigned long long& pd,
+                                           unsigned long long& po, bool& fresh, int& dfar, uint32_t& app) {
+  relax_edge_rec<kNF>(p, md, t, cost, du, ldcg_vrec(&p.ws.vrec[t]), nv, pd, po, fresh, dfar, app);
+}
+
 // Relax-list entry `slot` covers edges [base, base + deg) of the phase's edge
 // sequence: it owns the first edge of every tile that starts in that range.
 __device__ __forceinline__ void mark_tile_owner(uint32_t* owner, uint32_t slot, uint32_t base, uint32_t deg) {
@@ -365,11 +470,33 @@ __device__ __forceinline__ void mark_tile_owner(uint32_t* owner, uint32_t slot, 
   for (uint64_t t = ((uint64_t)base + kTile - 1) / kTile; t * kTile < end; ++t) owner[t] = slot;
 }
 
+// Start-of-phase values every block reads once, right after the previous
+// phase's last barrier (or a refill's or pull's): the queue length, the far
+// part of F, and the fused thresholds with the minima of the far vertices a
+// refill or pull of this phase moved to the queue (a_min_*, kInf64 otherwise).
+// (After a pull only the group leader's far count is current; no other block
+// uses it.)
+struct PhaseHead {
+  uint32_t nQ;
+  uint32_t far;
+  unsigned long long min_d, min_out;
+};
+
+__device__ __forceinline__ PhaseHead load_head(const Ctl* ctl, uint64_t k) {
+  const PhaseSlot* S0 = &ctl->slot[k % 4];
+  PhaseHead h;
+  h.nQ = ldcg_u32(&S0->qcount);
+  h.far = ldcg_u32(&ctl->far_count);
+  h.min_d = min(ldcg_u64(&S0->min_d), ldcg_u64(&S0->a_min_d));
+  h.min_out = min(ldcg_u64(&S0->min_out), ldcg_u64(&S0->a_min_out));
+  return h;
+}
+
 // ---------------------------------------------------------------------------
 // Step B of phase k (after step A for the three-step kind), by every block of
 // the group, ending with a group barrier.  Returns false if a barrier gave up.
-__device__ bool phase_select(const SolveParams& p, const Grp& grp, const Mode& md, const Arm arm, uint64_t k,
-                             const Shared& sh, Stats& st) {
+__device__ __noinline__ bool phase_select(const SolveParams& p, const Grp& grp, const Mode& md, const Arm arm, uint64_t k,
+                                          const PhaseHead& h, const Shared& sh, Stats& st) {
   const GraphView& g = p.g;
   const SolveWS& w = p.ws;
   Ctl* ctl = w.ctl;
@@ -384,12 +511,12 @@ __device__ bool phase_select(const SolveParams& p, const Grp& grp, const Mode& m
   uint32_t* Qn = w.q[cur ^ 1];
   PhaseSlot* S0 = &ctl->slot[k % 4];
   PhaseSlot* S1 = &ctl->slot[(k + 1) % 4];
-  const uint32_t nF = ldcg_u32(&S0->qcount);
+  const uint32_t nF = h.nQ;
   const bool dense = arm.dense;
   const bool in_dyn = md.use_in && arm.in_simple && w.cur_in != nullptr;
   if (leader) {
     reset_slot(&ctl->slot[(k + 2) % 4]);
-    const uint32_t fs = nF + (md.nearfar ? ldcg_u32(&ctl->far_count) : 0u);
+    const uint32_t fs = nF + (md.nearfar ? h.far : 0u);
     S0->fsize = fs;
     st.sum_f += fs;
     if (w.trace) S0->t_start = globaltimer_ns();
@@ -398,8 +525,8 @@ __device__ bool phase_select(const SolveParams& p, const Grp& grp, const Mode& m
   // ---- thresholds
   unsigned long long minD, minOut, min_apx = kInf64;
   if (md.fused) {
-    minD = ldcg_u64(&S0->min_d);
-    minOut = ldcg_u64(&S0->min_out);
+    minD = h.min_d;
+    minOut = h.min_out;
     if (in_dyn) {
       // A': dynamic in-minima against S at the start of the phase (no vertex of
       // this phase is marked before the barrier).  Cursors only move forward,
@@ -509,20 +636,26 @@ __device__ bool phase_select(const SolveParams& p, const Grp& grp, const Mode& m
   }
 
   // ---- B: select S', mark settled, build the relax list, compact the rest of F.
-  // Each block takes contiguous chunks of kSelItems * blockDim entries; all of a
-  // thread's record gathers are in flight together, and the chunk's kept
-  // entries and relax-list entries are placed with block scans and one atomic
-  // per chunk and output (coalesced writes, no per-warp contention).
+  // Warp-centric: each warp of the group takes chunks of 32 * kSelItems
+  // consecutive entries (lane-interleaved, so the queue loads are coalesced),
+  // with all of a lane's record gathers in flight together.  The kept entries
+  // and the relax-list entries of a chunk get their slots from one atomicAdd
+  // each by lane 0 (the relax list's slots and edge range from one packed
+  // 64-bit add, so the edge prefix is monotone in the slot); there is no block
+  // barrier inside the loop, so the warps of a block stream independently.
   unsigned long long pd = kInf64, po = kInf64;  // fused partials for phase k+1
   const uint64_t total = dense ? n : nF;
-  const uint64_t chunk = (uint64_t)nthr * kSelItems;
+  const unsigned int nwarps = nthr >> 5, warp = tid >> 5;
+  const uint64_t gwarps = (uint64_t)grp.size * nwarps;
+  const uint64_t wchunk = 32ull * kSelItems;
+  const unsigned int lt = (1u << lane) - 1u;
   uint32_t settled_here = 0;
-  for (uint64_t c0 = (uint64_t)grp.rank * chunk; c0 < total; c0 += (uint64_t)grp.size * chunk) {
+  for (uint64_t c0 = ((uint64_t)grp.rank * nwarps + warp) * wchunk; c0 < total; c0 += gwarps * wchunk) {
     uint32_t vv[kSelItems];
     bool ok[kSelItems];
 #pragma unroll
     for (int j = 0; j < kSelItems; ++j) {
-      const uint64_t i = c0 + (uint64_t)j * nthr + tid;
+      const uint64_t i = c0 + (uint64_t)j * 32 + lane;
       ok[j] = i < total;
       vv[j] = ok[j] ? (dense ? (uint32_t)i : ldcg_u32(&Q[i])) : 0u;
     }
@@ -582,43 +715,76 @@ __device__ bool phase_select(const SolveParams& p, const Grp& grp, const Mode& m
       }
     }
     settled_here += __popc(selm);
-    uint32_t nrel = 0, erel = 0;
+    // slots: entries of step j come before those of step j + 1, lanes in order
+    uint32_t kb[kSelItems], rb[kSelItems], eincl[kSelItems];
+    uint32_t nk = 0, nr = 0, ne = 0;
 #pragma unroll
-    for (int j = 0; j < kSelItems; ++j)
-      if (((selm >> j) & 1u) && rd[j].y > 0) {
-        ++nrel;
-        erel += rd[j].y;
-      }
-    uint32_t tk, tr, te;
-    const uint32_t pk = block_exclusive_scan(__popc(keepm), sh.scan, &tk);
-    const uint32_t pr = block_exclusive_scan(nrel, sh.scan, &tr);
-    const uint32_t pe = block_exclusive_scan(erel, sh.scan, &te);
-    if (tid == 0) {
-      sh.bases[0] = tk ? atomicAdd(&S1->qcount, tk) : 0u;
-      sh.bases[1] = tr ? atomicAdd(&S0->relax_packed, ((unsigned long long)tr << 32) | te) : 0ull;
+    for (int j = 0; j < kSelItems; ++j) {
+      const bool rl = ((selm >> j) & 1u) && rd[j].y > 0;
+      kb[j] = __ballot_sync(0xFFFFFFFFu, (keepm >> j) & 1u);
+      rb[j] = __ballot_sync(0xFFFFFFFFu, rl);
+      eincl[j] = rb[j] ? warp_inclusive_scan(rl ? rd[j].y : 0u) : 0u;
+      nk += __popc(kb[j]);
+      nr += __popc(rb[j]);
+      ne += __shfl_sync(0xFFFFFFFFu, eincl[j], 31);
     }
-    __syncthreads();
-    uint32_t kslot = (uint32_t)sh.bases[0] + pk;
-    const unsigned long long rb = sh.bases[1];
-    uint32_t rslot = (uint32_t)(rb >> 32) + pr;
-    uint32_t ebase = (uint32_t)rb + pe;
+    unsigned int kbase = 0;
+    unsigned long long rbase = 0;
+    if (lane == 0) {
+      if (nk) kbase = atomicAdd(&S1->qcount, nk);
+      if (nr) rbase = atomicAdd(&S0->relax_packed, ((unsigned long long)nr << 32) | ne);
+    }
+    kbase = __shfl_sync(0xFFFFFFFFu, kbase, 0);
+    rbase = __shfl_sync(0xFFFFFFFFu, rbase, 0);
+    uint32_t rslot = (uint32_t)(rbase >> 32), ebase = (uint32_t)rbase;
+    // relax-list entries spanning several tiles mark the later tiles' owners
+    // together with the warp (a hub's row can span thousands of tiles)
+    uint32_t wide = 0;
 #pragma unroll
     for (int j = 0; j < kSelItems; ++j) {
       if ((keepm >> j) & 1u) {
-        if (kslot < n) Qn[kslot] = vv[j];
+        const uint32_t slot = kbase + __popc(kb[j] & lt);
+        if (slot < n) Qn[slot] = vv[j];
         else atomicCAS(&ctl->err, 0, (int)SSSP_ERR_INTERNAL);
-        ++kslot;
       }
-      if (((selm >> j) & 1u) && rd[j].y > 0) {
-        if (rslot < n) {
-          *reinterpret_cast<ulonglong2*>(&w.sp[rslot]) =
-              make_ulonglong2(rr[j].d, (unsigned long long)rd[j].x | ((unsigned long long)ebase << 32));
-          if (w.tile_owner) mark_tile_owner(w.tile_owner, rslot, ebase, rd[j].y);
+      kbase += __popc(kb[j]);
+      if ((rb[j] >> lane) & 1u) {
+        const uint32_t slot = rslot + __popc(rb[j] & lt);
+        const uint32_t eb = ebase + eincl[j] - rd[j].y;
+        if (slot < n) {
+          *reinterpret_cast<ulonglong2*>(&w.sp[slot]) =
+              make_ulonglong2(rr[j].d, (unsigned long long)rd[j].x | ((unsigned long long)eb << 32));
+          if (w.tile_owner) {
+            const uint64_t t0 = ((uint64_t)eb + kTile - 1) / kTile;  // first tile starting inside [eb, eb + deg)
+            if (t0 * kTile < (uint64_t)eb + rd[j].y) {
+              w.tile_owner[t0] = slot;
+              if ((t0 + 1) * kTile < (uint64_t)eb + rd[j].y) wide |= 1u << j;
+            }
+          }
         } else {
           atomicCAS(&ctl->err, 0, (int)SSSP_ERR_INTERNAL);
         }
-        ++rslot;
-        ebase += rd[j].y;
+      }
+      rslot += __popc(rb[j]);
+      ebase += __shfl_sync(0xFFFFFFFFu, eincl[j], 31);
+    }
+    if (w.tile_owner && __any_sync(0xFFFFFFFFu, wide != 0)) {
+      // recompute each wide entry's slot and edge range and share it
+      uint32_t rs = (uint32_t)(rbase >> 32), es = (uint32_t)rbase;
+#pragma unroll
+      for (int j = 0; j < kSelItems; ++j) {
+        unsigned int wm = __ballot_sync(0xFFFFFFFFu, (wide >> j) & 1u);
+        while (wm) {
+          const int src = __ffs(wm) - 1;
+          wm &= wm - 1;
+          const uint32_t slot = rs + __popc(rb[j] & ((1u << src) - 1u));
+          const uint32_t eb = es + __shfl_sync(0xFFFFFFFFu, eincl[j] - rd[j].y, src);
+          const uint32_t deg = __shfl_sync(0xFFFFFFFFu, rd[j].y, src);
+          const uint64_t end = (uint64_t)eb + deg;
+          for (uint64_t t = ((uint64_t)eb + kTile - 1) / kTile + 1 + lane; t * kTile < end; t += 32) w.tile_owner[t] = slot;
+        }
+        rs += __popc(rb[j]);
+        es += __shfl_sync(0xFFFFFFFFu, eincl[j], 31);
       }
     }
   }
@@ -631,9 +797,17 @@ __device__ bool phase_select(const SolveParams& p, const Grp& grp, const Mode& m
 // Step C of phase k (relax every out-edge of S', edge-balanced tiles), then
 // the end-of-phase barrier, counters and trace.  Every block of the group
 // calls it.  Returns false if a barrier gave up.
+//
+// Warp-centric: each warp takes tiles of kTile consecutive edges of the relax
+// list's edge sequence.  The relax-list entries overlapping a tile (found with
+// the tile-owner marks of step B, or by a warp search without them) are staged
+// in the warp's own shared-memory slice; every lane then finds the owner of
+// each of its kRelaxItems edges by binary search there, issues all of its edge
+// loads, then all of its target-record loads, and relaxes.  Vertices new to
+// the next queue get their slots from one atomicAdd per tile.
 template <bool kNF>
-__device__ bool phase_relax(const SolveParams& p, const Grp& grp, const Mode& md, const Arm arm, uint64_t k,
-                            unsigned long long bound, bool resumed, const Shared& sh, Stats& st) {
+__device__ __noinline__ bool phase_relax(const SolveParams& p, const Grp& grp, const Mode& md, const Arm arm, uint64_t k,
+                                         const NfView& nv, bool resumed, const Shared& sh, Stats& st) {
   const GraphView& g = p.g;
   const SolveWS& w = p.ws;
   Ctl* ctl = w.ctl;
@@ -647,81 +821,118 @@ __device__ bool phase_relax(const SolveParams& p, const Grp& grp, const Mode& md
   PhaseSlot* S1 = &ctl->slot[(k + 1) % 4];
   unsigned long long pd = kInf64, po = kInf64;
   int dfar = 0;
+  const unsigned int nwarps = nthr >> 5;
+  const uint64_t gwarps = (uint64_t)grp.size * nwarps;
+  // the owner marks of the warp's first tile are loaded together with the
+  // list's size (unused if the tile lies past the phase's edges)
+  const uint64_t tile0 = (uint64_t)grp.rank * nwarps + warp;
+  uint32_t own0 = 0, own1 = 0;
+  if (w.tile_owner && tile0 + 1 < g.m / kTile + 2) {
+    own0 = ldcg_u32(&w.tile_owner[tile0]);
+    own1 = ldcg_u32(&w.tile_owner[tile0 + 1]);
+  }
   const unsigned long long packed = ldcg_u64(&S0->relax_packed);
   const uint32_t nS = (uint32_t)(packed >> 32);
   const uint32_t E = (uint32_t)packed;
   if (leader && w.trace && !resumed) S0->t_select = globaltimer_ns();  // (a hand-off set it)
-  for (uint64_t tile = grp.rank; tile * kTile < E; tile += grp.size) {
+  const unsigned int lt = (1u << lane) - 1u;
+  uint32_t* s_base = sh.s_base + warp * kTile;
+  uint32_t* s_row = sh.s_row + warp * kTile;
+  unsigned long long* s_d = sh.s_d + warp * kTile;
+  for (uint64_t tile = tile0; tile * kTile < E; tile += gwarps) {
     const uint32_t e0 = (uint32_t)(tile * kTile);
     const uint32_t e1 = (uint64_t)e0 + kTile < E ? e0 + kTile : E;
-    if (warp == 0) {
-      uint32_t lo = 0, hi = nS - 1;
-      if (w.tile_owner) {
-        // entries lo .. hi intersect the tile (hi may start just past it, and is
-        // then dropped by the kTile cap below: the per-edge search never picks it)
-        lo = ldcg_u32(&w.tile_owner[tile]);
-        if (e1 < E) hi = ldcg_u32(&w.tile_owner[tile + 1]);
-      } else if (!(e0 == 0 && e1 == E)) {
-        lo = warp_upper_bound_sp(w.sp, nS, e0) - 1;
-        hi = warp_upper_bound_sp(w.sp, nS, e1 - 1) - 1;
-      }
-      if (lane == 0) { sh.s_range[0] = lo; sh.s_range[1] = hi; }
+    uint32_t lo = 0, hi = nS - 1;
+    if (w.tile_owner) {
+      // entries lo .. hi intersect the tile (hi may start just past it, and is
+      // then dropped by the kTile cap below: the per-edge search never picks it)
+      lo = tile == tile0 ? own0 : ldcg_u32(&w.tile_owner[tile]);
+      if (e1 < E) hi = tile == tile0 ? own1 : ldcg_u32(&w.tile_owner[tile + 1]);
+    } else if (!(e0 == 0 && e1 == E)) {
+      lo = warp_upper_bound_sp(w.sp, nS, e0) - 1;
+      hi = warp_upper_bound_sp(w.sp, nS, e1 - 1) - 1;
     }
-    __syncthreads();
-    const uint32_t lo = sh.s_range[0];
-    const uint32_t cnt = min(sh.s_range[1] - sh.s_range[0] + 1, (uint32_t)kTile);
-    for (uint32_t j = tid; j < cnt; j += nthr) {
+    const uint32_t cnt = min(hi - lo + 1, (uint32_t)kTile);
+    for (uint32_t j = lane; j < cnt; j += 32) {
       const SpEnt e = ldcg_sp(&w.sp[lo + j]);
-      sh.s_base[j] = e.base;
-      sh.s_row[j] = e.row;
-      sh.s_d[j] = e.d;
+      s_base[j] = e.base;
+      s_row[j] = e.row;
+      s_d[j] = e.d;
     }
-    __syncthreads();
-    uint32_t fv[kRelaxItems];
-    uint32_t fmask = 0;
+    __syncwarp();
+    uint2 ed[kRelaxItems];
+    uint32_t own[kRelaxItems];  // owner entry in the staged slice (its d is read again at the relaxation)
+    uint32_t valid = 0;
 #pragma unroll
     for (int it = 0; it < kRelaxItems; ++it) {
-      const uint32_t e = e0 + it * nthr + tid;
-      fv[it] = 0;
+      const uint32_t e = e0 + it * 32 + lane;
+      ed[it] = make_uint2(0, 0);
+      own[it] = 0;
       if (e < e1) {
         uint32_t a = 0, b = cnt;  // owner = last j with s_base[j] <= e
         while (b - a > 1) {
           const uint32_t mid = (a + b) >> 1;
-          if (sh.s_base[mid] <= e) a = mid; else b = mid;
+          if (s_base[mid] <= e) a = mid; else b = mid;
         }
-        const uint2 ed = __ldg(&g.edges[sh.s_row[a] + (e - sh.s_base[a])]);
-        bool fresh = false;
-        relax_edge<kNF>(p, md, ed.x, ed.y, sh.s_d[a], bound, pd, po, fresh, dfar);
-        if (fresh) {
-          fv[it] = ed.x;
-          fmask |= 1u << it;
-        }
+        ed[it] = __ldg(&g.edges[s_row[a] + (e - s_base[a])]);
+        own[it] = a;
+        valid |= 1u << it;
       }
     }
-    // vertices new to F: one block scan and one atomic per tile (APPROX also
-    // lists them for the next phase's bookkeeping)
-    uint32_t tf;
-    const uint32_t pf = block_exclusive_scan(__popc(fmask), sh.scan, &tf);
-    if (tid == 0) {
-      sh.bases[0] = tf ? atomicAdd(&S1->qcount, tf) : 0u;
-      if (md.approx) sh.bases[1] = tf ? atomicAdd(&S1->fresh_count, tf) : 0u;
-    }
-    __syncthreads();
-    uint32_t fslot = (uint32_t)sh.bases[0] + pf;
-    uint32_t xslot = md.approx ? (uint32_t)sh.bases[1] + pf : 0u;
+    VRec rt[kRelaxItems];
 #pragma unroll
     for (int it = 0; it < kRelaxItems; ++it)
-      if ((fmask >> it) & 1u) {
-        if (fslot < n) Qn[fslot] = fv[it];
-        else atomicCAS(&ctl->err, 0, (int)SSSP_ERR_INTERNAL);
-        ++fslot;
-        if (md.approx) {
-          if (xslot < n) w.fresh[xslot] = fv[it];
-          else atomicCAS(&ctl->err, 0, (int)SSSP_ERR_INTERNAL);
-          ++xslot;
-        }
+      if ((valid >> it) & 1u) rt[it] = ldcg_vrec(&w.vrec[ed[it].x]);
+    uint32_t fmask = 0;
+    uint32_t app[kRelaxItems];
+#pragma unroll
+    for (int it = 0; it < kRelaxItems; ++it) {
+      app[it] = kNoBucket;
+      if ((valid >> it) & 1u) {
+        bool fresh = false;
+        relax_edge_rec<kNF>(p, md, ed[it].x, ed[it].y, s_d[own[it]], rt[it], nv, pd, po, fresh, dfar, app[it]);
+        if (fresh) fmask |= 1u << it;
       }
-    __syncthreads();
+    }
+    if (kNF) {
+      uint32_t tv[kRelaxItems];
+#pragma unroll
+      for (int it = 0; it < kRelaxItems; ++it) tv[it] = ed[it].x;
+      nf_list_append_n<kRelaxItems>(nv, app, tv);
+    }
+    // vertices new to F: one atomic per tile (APPROX also lists them for the
+    // next phase's bookkeeping)
+    uint32_t fb[kRelaxItems];
+    uint32_t nfr = 0;
+#pragma unroll
+    for (int it = 0; it < kRelaxItems; ++it) {
+      fb[it] = __ballot_sync(0xFFFFFFFFu, (fmask >> it) & 1u);
+      nfr += __popc(fb[it]);
+    }
+    if (nfr) {
+      unsigned int fslot = 0, xslot = 0;
+      if (lane == 0) {
+        fslot = atomicAdd(&S1->qcount, nfr);
+        if (md.approx) xslot = atomicAdd(&S1->fresh_count, nfr);
+      }
+      fslot = __shfl_sync(0xFFFFFFFFu, fslot, 0);
+      xslot = __shfl_sync(0xFFFFFFFFu, xslot, 0);
+#pragma unroll
+      for (int it = 0; it < kRelaxItems; ++it) {
+        if ((fmask >> it) & 1u) {
+          const uint32_t off = __popc(fb[it] & lt);
+          if (fslot + off < n) Qn[fslot + off] = ed[it].x;
+          else atomicCAS(&ctl->err, 0, (int)SSSP_ERR_INTERNAL);
+          if (md.approx) {
+            if (xslot + off < n) w.fresh[xslot + off] = ed[it].x;
+            else atomicCAS(&ctl->err, 0, (int)SSSP_ERR_INTERNAL);
+          }
+        }
+        fslot += __popc(fb[it]);
+        xslot += __popc(fb[it]);
+      }
+    }
+    __syncwarp();  // the staged entries are read before the next tile overwrites them
   }
   if (md.fused) block_min2_to_global(pd, po, &S1->min_d, md.use_out ? &S1->min_out : nullptr, sh.red);
   if (kNF) {  // far-part count: one atomic per block (the barrier above orders scratch reuse)
@@ -742,8 +953,9 @@ __device__ bool phase_relax(const SolveParams& p, const Grp& grp, const Mode& md
       sssp_phase_record r;
       r.frontier = ldcg_u32(&S0->fsize);
       r.settled = settled_now;
-      r.min_d = md.fused ? ldcg_u64(&S0->min_d) : ldcg_u64(&S0->a_min_d);
-      r.min_out = md.use_out ? (md.fused ? ldcg_u64(&S0->min_out) : ldcg_u64(&S0->a_min_out))
+      r.min_d = md.fused ? min(ldcg_u64(&S0->min_d), ldcg_u64(&S0->a_min_d)) : ldcg_u64(&S0->a_min_d);
+      r.min_out = md.use_out ? (md.fused ? min(ldcg_u64(&S0->min_out), ldcg_u64(&S0->a_min_out))
+                                         : ldcg_u64(&S0->a_min_out))
                              : (md.approx ? ldcg_u64(&S0->a_min_apx) : kInf64);
       r.deg_settled = E;
       uint32_t c = p.crit & SSSP_CRITERIA_MASK;
@@ -761,16 +973,20 @@ __device__ bool phase_relax(const SolveParams& p, const Grp& grp, const Mode& md
 }
 
 __device__ __forceinline__ bool run_phase(const SolveParams& p, const Grp& grp, const Mode& md, uint64_t k,
-                                          unsigned long long bound, uint32_t nf_code, const Shared& sh, Stats& st) {
-  const PhaseSlot* prev = &p.ws.ctl->slot[(k + 3) % 4];
-  const uint32_t nQ = ldcg_u32(&p.ws.ctl->slot[k % 4].qcount);
-  const uint32_t nF = nQ + (md.nearfar ? ldcg_u32(&p.ws.ctl->far_count) : 0u);
-  const Arm arm = choose_arm(p, k, nQ, nF, (uint32_t)ldcg_u64(&prev->relax_packed), ldcg_u32(&prev->settled_now),
-                             ldcg_u32(&prev->fsize), bound != kNoBound);
+                                          const NfView& nv, uint32_t nf_code, const PhaseHead& h, const Shared& sh,
+                                          Stats& st) {
+  Arm arm;
+  if ((p.crit & SSSP_POLICY_LEARNED) && p.policy != nullptr) {  // (the previous phase's counts are its features)
+    const PhaseSlot* prev = &p.ws.ctl->slot[(k + 3) % 4];
+    arm = choose_arm(p, k, h.nQ, h.nQ + (md.nearfar ? h.far : 0u), (uint32_t)ldcg_u64(&prev->relax_packed),
+                     ldcg_u32(&prev->settled_now), ldcg_u32(&prev->fsize), nv.bound != kNoBound);
+  } else {
+    arm = arm_for(p, h.nQ);
+  }
   if (grp.rank == 0 && threadIdx.x == 0) p.ws.ctl->slot[k % 4].arm = arm_code(arm, grp.size == 1) | nf_code;
-  if (!phase_select(p, grp, md, arm, k, sh, st)) return false;
-  return bound != kNoBound ? phase_relax<true>(p, grp, md, arm, k, bound, false, sh, st)
-                           : phase_relax<false>(p, grp, md, arm, k, bound, false, sh, st);
+  if (!phase_select(p, grp, md, arm, k, h, sh, st)) return false;
+  return nv.bound != kNoBound ? phase_relax<true>(p, grp, md, arm, k, nv, false, sh, st)
+                              : phase_relax<false>(p, grp, md, arm, k, nv, false, sh, st);
 }
 
 // Relax step of a solo phase: the warps of the block stride over the relax
@@ -788,13 +1004,13 @@ struct SoloRelax {
 
 template <bool kNF>
 __device__ __forceinline__ void solo_relax(const SolveParams& p, const Mode& md, const SoloRelax& r,
-                                           unsigned long long bound, unsigned long long& pd, unsigned long long& po,
+                                           const NfView& nv, unsigned long long& pd, unsigned long long& po,
                                            int& dfar) {
   const unsigned int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (uint32_t eb = warp * 32; eb < r.E; eb += blockDim.x) {
     const uint32_t e = eb + lane;
     bool fresh = false;
-    uint32_t t = 0;
+    uint32_t t = 0, app = kNoBucket;
     if (e < r.E) {
       uint32_t a = 0, b = r.nS;
       while (b - a > 1) {
@@ -803,8 +1019,9 @@ __device__ __forceinline__ void solo_relax(const SolveParams& p, const Mode& md,
       }
       const uint2 ed = __ldg(&p.g.edges[r.sp_row[a] + (e - r.sp_base[a])]);
       t = ed.x;
-      relax_edge<kNF>(p, md, t, ed.y, r.sp_d[a], bound, pd, po, fresh, dfar);
+      relax_edge<kNF>(p, md, t, ed.y, r.sp_d[a], nv, pd, po, fresh, dfar, app);
     }
+    if (kNF) nf_list_append(nv, app, t);
     const unsigned int fmask = __ballot_sync(0xFFFFFFFFu, fresh);
     if (fmask) {
       unsigned int b0 = 0;
@@ -832,7 +1049,7 @@ __device__ __forceinline__ void solo_relax(const SolveParams& p, const Mode& md,
 // slot[k%3].  Exit at phase k: the same state with slot[(k+1)%3] reset (no
 // handoff), or the state after a grid selection step of phase k (handoff).
 // All threads of the block call it.
-__device__ uint64_t solo_episode(const SolveParams& p, const Mode& md, uint64_t k, unsigned long long bound,
+__device__ uint64_t solo_episode(const SolveParams& p, const Mode& md, uint64_t k, const NfView& nv,
                                  uint32_t nf_code, unsigned char* smem, Stats& st_shared, bool can_handoff,
                                  bool* handoff) {
   const GraphView& g = p.g;
@@ -863,13 +1080,13 @@ __device__ uint64_t solo_episode(const SolveParams& p, const Mode& md, uint64_t 
   uint64_t s_prev = ldcg_u32(&ctl->slot[(k + 3) % 4].settled_now);
   uint64_t f_prev = ldcg_u32(&ctl->slot[(k + 3) % 4].fsize);
   uint32_t nF = ldcg_u32(&ctl->slot[k % 4].qcount);
-  const bool kNF = bound != kNoBound;
+  const bool kNF = nv.bound != kNoBound;
   uint32_t far = kNF ? ldcg_u32(&ctl->far_count) : 0u;  // far part of F (not in the queues)
   Stats st = st_shared;  // thread 0's running counters, in registers for the episode
   Arm arm{false, false, -1};
   unsigned int since_pick = 0;
-  unsigned long long minD = ldcg_u64(&ctl->slot[k % 4].min_d);
-  unsigned long long minOut = ldcg_u64(&ctl->slot[k % 4].min_out);
+  unsigned long long minD = min(ldcg_u64(&ctl->slot[k % 4].min_d), ldcg_u64(&ctl->slot[k % 4].a_min_d));
+  unsigned long long minOut = min(ldcg_u64(&ctl->slot[k % 4].min_out), ldcg_u64(&ctl->slot[k % 4].a_min_out));
   {
     const uint32_t* gq = w.q[(k - 1) & 1];
     uint32_t* sq = ((k - 1) & 1) ? sqb : sqa;
@@ -1075,8 +1292,8 @@ __device__ uint64_t solo_episode(const SolveParams& p, const Mode& md, uint64_t 
     po = kInf64;
     int dfar = 0;
     const SoloRelax sr{sp_d, sp_row, sp_base, nS, E, sqn, gqn, &s_qn};
-    if (kNF) solo_relax<true>(p, md, sr, bound, pd, po, dfar);
-    else solo_relax<false>(p, md, sr, bound, pd, po, dfar);
+    if (kNF) solo_relax<true>(p, md, sr, nv, pd, po, dfar);
+    else solo_relax<false>(p, md, sr, nv, pd, po, dfar);
     pd = warp_min_u64(pd);
     po = warp_min_u64(po);
     if (kNF) dfar = __reduce_add_sync(0xFFFFFFFFu, dfar);
@@ -1111,7 +1328,7 @@ __device__ uint64_t solo_episode(const SolveParams& p, const Mode& md, uint64_t 
         w.trace[k - 1] = r;
       }
     }
-    nf_code &= ~kArmNfRefill;  // a refill or split only runs before the episode
+    nf_code &= ~(kArmNfRefill | kArmNfPull);  // a refill, pull or split only runs before the episode
     minD = s_thr_d;
     minOut = s_thr_o;
     e_prev = E;
@@ -1123,7 +1340,7 @@ __device__ uint64_t solo_episode(const SolveParams& p, const Mode& md, uint64_t 
     __syncthreads();  // shared counters are read before the next phase resets them
     if (nF == 0 || nF > cap || k > (uint64_t)n + 1) break;
     // thresholds above the bound are exact only after the far part is scanned
-    if (kNF && far > 0 && (md.use_out ? minOut : minD) > bound) break;
+    if (kNF && far > 0 && (md.use_out ? minOut : minD) > nv.bound) break;
   }
   // hand the state back in global memory for phase k
   {
@@ -1191,9 +1408,15 @@ __device__ __forceinline__ uint32_t nf_target(const SolveParams& p, uint64_t k, 
   uint32_t t = p.nf_target;
   if (t == 0) {
     const uint32_t s_prev = ldcg_u32(&p.ws.ctl->slot[(k + 3) % 4].settled_now);
-    const float s = (float)(s_prev > 256u ? s_prev : 256u);
-    const float x = 2.0f * sqrtf((float)p.g.n * s);
-    t = x < 4096.0f ? 4096u : (x > (float)p.g.n ? p.g.n : (uint32_t)x);
+    if (p.ws.nf_list) {
+      // listed buckets: raising B costs a pass over the pulled lists only, so
+      // the near part is kept at a few phases' worth of settled vertices
+      t = s_prev > 2048u ? 4u * s_prev : 8192u;
+    } else {
+      const float s = (float)(s_prev > 256u ? s_prev : 256u);
+      const float x = 2.0f * sqrtf((float)p.g.n * s);
+      t = x < 4096.0f ? 4096u : (x > (float)p.g.n ? p.g.n : (uint32_t)x);
+    }
   }
   const uint32_t cap = fringe / 8 > 0 ? fringe / 8 : 1u;
   return t < cap ? t : cap;
@@ -1234,12 +1457,40 @@ __device__ __forceinline__ int nf_pick_bin(const unsigned int* gh, uint32_t targ
   return b;
 }
 
+// Bucket geometry set by a split or a full refill: bound B, bucket width 2^s
+// with 2^s <= e + 1 (e: the key offset above the old bound holding about
+// `target` vertices), origin O = B + 1 - 2^s (the near part is bucket 0 and
+// below), cursor 0.
+__device__ __forceinline__ NfView nf_geometry(const NfView& nv, unsigned long long B, unsigned long long e) {
+  NfView v = nv;
+  v.bound = B;
+  v.cursor = 0;
+  v.origin = 0;
+  v.shift = 0;
+  if (B < kNoBound) {
+    const unsigned long long w1 = (e < B ? e : B) + 1;
+    v.shift = 63u - (uint32_t)__clzll((long long)w1);
+    v.origin = B + 1 - (1ull << v.shift);
+  }
+  return v;
+}
+
+// Empties the bucket lists before a split or a full refill lists the far
+// part anew (block rank 0 of the group; ordered before any listing by the
+// group barrier that follows).
+__device__ __forceinline__ void nf_lists_reset(const Grp& grp, Ctl* ctl) {
+  if (grp.rank == 0) {
+    if (threadIdx.x < kNfRing) ctl->nf_cnt[threadIdx.x] = 0;
+    if (threadIdx.x == 0) ctl->nf_beyond = kInf32;
+  }
+}
+
 // First split (B = kNoBound, no far vertex, so the phase-k thresholds are
 // exact): B = T + the key offset below which about `target` queue entries lie;
 // entries above B are marked far and the queue is compacted.  Leaves B as is
 // when the whole fringe fits the target.  Every block of the group calls it.
 __device__ __noinline__ bool nf_split(const SolveParams& p, const Grp& grp, const Mode& md, uint64_t k, const Shared& sh,
-                         unsigned long long& bound, uint32_t& uses) {
+                                      NfView& nv, uint32_t& uses) {
   const SolveWS& w = p.ws;
   Ctl* ctl = w.ctl;
   const unsigned int tid = threadIdx.x, nthr = blockDim.x;
@@ -1267,6 +1518,7 @@ __device__ __noinline__ bool nf_split(const SolveParams& p, const Grp& grp, cons
   nf_hist_flush(hist, gh);
   if (leader) ctl->nf_tmp = 0;
   if (tid < kNfBins && grp.rank == 0) ctl->hist[(uses + 1) & 1][tid] = 0;  // the next use's histogram
+  nf_lists_reset(grp, ctl);
   ++uses;
   if (!grp.sync()) return false;
   const int b = nf_pick_bin(gh, nf_target(p, k, nF), sh);
@@ -1274,14 +1526,15 @@ __device__ __noinline__ bool nf_split(const SolveParams& p, const Grp& grp, cons
   const unsigned long long e = nf_bin_upper(b);
   const unsigned long long B = e >= kNoBound - T ? kNoBound : T + e;
   if (B >= kNoBound) return true;
+  const NfView v2 = nf_geometry(nv, B, e);
   // keep the entries with key <= B (compacted into the relax-list buffer),
-  // mark the others far
+  // mark the others far and list them in their buckets
   uint32_t* tmp = reinterpret_cast<uint32_t*>(w.sp);
   uint32_t demoted = 0;
   for (uint64_t c0 = (uint64_t)grp.rank * nthr; c0 < nF; c0 += gthreads) {
     const uint64_t i = c0 + tid;
     bool keep = false;
-    uint32_t v = 0;
+    uint32_t v = 0, app = kNoBucket;
     if (i < nF) {
       v = ldcg_u32(&Q[i]);
       const VRec r = ldcg_vrec(&w.vrec[v]);
@@ -1289,8 +1542,10 @@ __device__ __noinline__ bool nf_split(const SolveParams& p, const Grp& grp, cons
       if (!keep) {
         w.vrec[v].d = r.d | kFarBit;
         ++demoted;
+        if (v2.lists) app = nf_bucket(v2, r.d, r.im);
       }
     }
+    nf_list_append(v2, app, v);
     uint32_t tk;
     const uint32_t pk = block_exclusive_scan(keep ? 1u : 0u, sh.scan, &tk);
     if (tid == 0) sh.bases[0] = tk ? atomicAdd(&ctl->nf_tmp, tk) : 0u;
@@ -1305,7 +1560,7 @@ __device__ __noinline__ bool nf_split(const SolveParams& p, const Grp& grp, cons
   const uint32_t kept = ldcg_u32(&ctl->nf_tmp);
   for (uint64_t i = gtid; i < kept; i += gthreads) Q[i] = ldcg_u32(&tmp[i]);
   if (leader) S0->qcount = kept;
-  bound = B;
+  if (tid == 0) nv = v2;  // (published to the block by the barrier below)
   return grp.sync();
 }
 
@@ -1321,7 +1576,7 @@ __device__ __noinline__ bool nf_split(const SolveParams& p, const Grp& grp, cons
 constexpr int kNfItems = 8;
 
 __device__ __noinline__ bool nf_refill(const SolveParams& p, const Grp& grp, const Mode& md, uint64_t k, const Shared& sh,
-                                       unsigned long long& bound, uint32_t& uses) {
+                                       NfView& nv, uint32_t& uses) {
   const GraphView& g = p.g;
   const SolveWS& w = p.ws;
   Ctl* ctl = w.ctl;
@@ -1338,6 +1593,7 @@ __device__ __noinline__ bool nf_refill(const SolveParams& p, const Grp& grp, con
   // both counts while slower ones still pick the bin (every block must pick
   // the same B)
   const uint32_t fringe = ldcg_u32(&S0->qcount) + ldcg_u32(&ctl->far_count);
+  const unsigned long long bound = nv.bound;
   // this block's vertex range [lo, hi)
   const uint64_t per = ((uint64_t)n + grp.size - 1) / grp.size;
   const uint64_t lo = (uint64_t)grp.rank * per;
@@ -1385,6 +1641,7 @@ __device__ __noinline__ bool nf_refill(const SolveParams& p, const Grp& grp, con
   const uint32_t cnt = s_fcnt;  // this block's far entries (the barrier above published it)
   nf_hist_flush(hist, gh);
   if (tid < kNfBins && grp.rank == 0) ctl->hist[(uses + 1) & 1][tid] = 0;
+  nf_lists_reset(grp, ctl);
   ++uses;
   if (!grp.sync()) return false;
   const unsigned long long a_d = ldcg_u64(&S0->min_d), f_d = ldcg_u64(&S0->a_min_d);
@@ -1396,26 +1653,31 @@ __device__ __noinline__ bool nf_refill(const SolveParams& p, const Grp& grp, con
   const unsigned long long e = b >= kNfBins ? kNoBound : nf_bin_upper(b);
   unsigned long long B = e >= kNoBound - bound ? kNoBound : bound + e;
   if (B < T) B = T >= kNoBound ? kNoBound : T;
+  const NfView v2 = nf_geometry(nv, B, e);
   uint32_t moved = 0;
   const uint32_t rchunk = nthr * kSelItems;
   for (uint32_t c0 = 0; c0 < cnt; c0 += rchunk) {
     uint32_t mv = 0;
-    uint32_t vv[kSelItems];
+    uint32_t vv[kSelItems], app[kSelItems];
 #pragma unroll
     for (int j = 0; j < kSelItems; ++j) {
       const uint32_t i = c0 + j * nthr + tid;
       vv[j] = 0;
+      app[j] = kNoBucket;
       if (i < cnt) {
         const ulonglong2 t = __ldcg(&tmp[lo + i]);
         const uint32_t im = (uint32_t)(t.y >> 32);
         const unsigned long long key = (im == kInf32 || t.x <= im) ? 0ull : t.x - im;
+        vv[j] = (uint32_t)t.y;
         if (key <= B) {
-          vv[j] = (uint32_t)t.y;
           w.vrec[vv[j]].d = t.x;
           mv |= 1u << j;
+        } else if (v2.lists) {
+          app[j] = nf_bucket(v2, t.x, im);
         }
       }
     }
+    nf_list_append_n<kSelItems>(v2, app, vv);
     uint32_t tm;
     const uint32_t pm = block_exclusive_scan(__popc(mv), sh.scan, &tm);
     if (tid == 0) sh.bases[0] = tm ? atomicAdd(&S0->qcount, tm) : 0u;
@@ -1438,8 +1700,137 @@ __device__ __noinline__ bool nf_refill(const SolveParams& p, const Grp& grp, con
     S0->min_d = minD;
     S0->min_out = minOut;
   }
-  bound = B;
+  __syncthreads();
+  if (tid == 0) nv = v2;  // (published to the block by the barrier below)
   return grp.sync();
+}
+
+// Pull (far part listed, accumulated T > B): raise B to the end of the bucket
+// holding T -- further, bucket by bucket, while the pulled lists hold fewer
+// than `target` entries -- and move every far vertex of the pulled lists whose
+// key is now <= B' to the queue of phase k (the one thread whose atomicAnd
+// clears the far bit moves it; stale and duplicate entries are skipped),
+// taking the minima of d and d + outmin over the moved vertices into the
+// phase's thresholds.  The vertex attaining T is among them or in the queue,
+// every far vertex left has key > B' >= T, so the thresholds stay exact.  Sets
+// *need_full (and changes nothing) when a full refill is needed instead: the
+// bucket holding T lies past the ring or at or after the lowest bucket with an
+// unlisted vertex.  Every block of the group calls it.
+__device__ __noinline__ bool nf_pull(const SolveParams& p, const Grp& grp, const Mode& md, uint64_t k, const Shared& sh,
+                                     NfView& nv, bool* need_full) {
+  const SolveWS& w = p.ws;
+  Ctl* ctl = w.ctl;
+  const uint32_t n = p.g.n;
+  const unsigned int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  PhaseSlot* S0 = &ctl->slot[k % 4];
+  uint32_t* Q = w.q[(k - 1) & 1];
+  __shared__ uint32_t s_pre[kNfRing + 1];
+  __shared__ uint32_t s_nb;
+  __shared__ unsigned long long s_newb;
+  // inputs no block changes before the barrier below (moved vertices' minima
+  // and count go to scratch fields first), so every block computes the same B'
+  const unsigned long long T = md.use_out ? ldcg_u64(&S0->min_out) : ldcg_u64(&S0->min_d);
+  const uint32_t beyond = ldcg_u32(&ctl->nf_beyond);
+  const uint32_t target = nf_target(p, k, kInf32);
+  const uint32_t c = nv.cursor;
+  if (tid == 0) {
+    s_nb = 0;
+    const unsigned long long bt = T >= kNoBound ? ~0ull : (T - nv.origin) >> nv.shift;  // T > B >= O
+    if (bt <= (unsigned long long)c + kNfRing && bt < beyond) {
+      uint32_t c1 = (uint32_t)bt;
+      uint64_t tot = 0;
+      s_pre[0] = 0;
+      for (uint32_t i = c + 1; i <= c1; ++i) {
+        const uint32_t f = ldcg_u32(&ctl->nf_cnt[i & (kNfRing - 1)]);
+        tot += f < nv.cap ? f : nv.cap;
+        s_pre[i - c] = (uint32_t)tot;
+      }
+      while (tot < target && c1 + 1 <= c + kNfRing && c1 + 1 < beyond) {
+        ++c1;
+        const uint32_t f = ldcg_u32(&ctl->nf_cnt[c1 & (kNfRing - 1)]);
+        tot += f < nv.cap ? f : nv.cap;
+        s_pre[c1 - c] = (uint32_t)tot;
+      }
+      // B' = O + (c1 + 1) * 2^s - 1, if it stays below kNoBound
+      const unsigned long long span = (unsigned long long)(c1 + 1);
+      if (nv.shift < 62 && span <= ((kNoBound - nv.origin) >> nv.shift)) {
+        s_nb = c1 - c;
+        s_newb = nv.origin + (span << nv.shift) - 1;
+      }
+    }
+  }
+  __syncthreads();
+  const uint32_t nb = s_nb;
+  if (nb == 0) {
+    *need_full = true;
+    return true;
+  }
+  const unsigned long long B1 = s_newb;
+  const uint32_t total = s_pre[nb];
+  unsigned long long lmin_d = kInf64, lmin_o = kInf64;
+  uint32_t moved = 0;
+  const uint64_t gwarps = (uint64_t)grp.size * (nthr >> 5);
+  for (uint64_t i0 = ((uint64_t)grp.rank * (nthr >> 5) + warp) * 32; i0 < total; i0 += gwarps * 32) {
+    const uint32_t i = (uint32_t)i0 + lane;
+    bool mv = false;
+    uint32_t v = 0;
+    if (i < total) {
+      uint32_t a = 0, b = nb;  // bucket j (0-based) with s_pre[j] <= i < s_pre[j + 1]
+      while (b - a > 1) {
+        const uint32_t mid = (a + b) >> 1;
+        if (s_pre[mid] <= i) a = mid; else b = mid;
+      }
+      const uint32_t slot = (c + 1 + a) & (kNfRing - 1);
+      v = ldcg_u32(&nv.lists[(uint64_t)slot * nv.cap + (i - s_pre[a])]);
+      const VRec r = ldcg_vrec(&w.vrec[v]);
+      if ((r.d >> 62) == 1u) {  // far (bit 62 set, bit 63 clear)
+        const unsigned long long d = r.d & ~kFarBit;
+        if (nf_key(r, d) <= B1) {
+          const unsigned long long old = atomicAnd(&w.vrec[v].d, ~kFarBit);
+          if (old & kFarBit) {
+            mv = true;
+            lmin_d = d < lmin_d ? d : lmin_d;
+            if (r.om != kInf32) {
+              const unsigned long long x = d + r.om;
+              lmin_o = x < lmin_o ? x : lmin_o;
+            }
+          }
+        }
+      }
+    }
+    const unsigned int mm = __ballot_sync(0xFFFFFFFFu, mv);
+    if (mm) {
+      unsigned int base = 0;
+      if (lane == 0) base = atomicAdd(&S0->qcount, (unsigned int)__popc(mm));
+      base = __shfl_sync(0xFFFFFFFFu, base, 0);
+      if (mv) {
+        const uint32_t slot = base + __popc(mm & ((1u << lane) - 1u));
+        if (slot < n) Q[slot] = v;
+        else atomicCAS(&ctl->err, 0, (int)SSSP_ERR_INTERNAL);
+      }
+      moved += __popc(mm);
+    }
+  }
+  // the selection step takes min(min_d, a_min_d) and min(min_out, a_min_out)
+  block_min2_to_global(lmin_d, lmin_o, &S0->a_min_d, md.use_out ? &S0->a_min_out : nullptr, sh.red);
+  if (lane == 0 && moved) atomicAdd(&ctl->nf_moved, moved);
+  if (!grp.sync()) return false;
+  if (grp.rank == 0) {
+    // the pulled slots start over as the buckets past the ring's far end (no
+    // block lists a far vertex before the next selection step's barrier)
+    if (tid >= 1 && tid <= nb) ctl->nf_cnt[(c + tid) & (kNfRing - 1)] = 0;
+    if (tid == 0) {
+      const uint32_t mv = ldcg_u32(&ctl->nf_moved);
+      if (mv) atomicSub(&ctl->far_count, mv);
+      ctl->nf_moved = 0;
+    }
+  }
+  if (tid == 0) {
+    nv.bound = B1;
+    nv.cursor = c + nb;
+  }
+  __syncthreads();
+  return true;
 }
 
 // Initialise, run all phases (switching to solo mode while the fringe is
@@ -1459,11 +1850,18 @@ __device__ void solve_body(const SolveParams& p, const Grp& grp, unsigned char* 
   // once per phase at most, and keeping them out of registers leaves the
   // phase loops more room.
   __shared__ Stats s_st;
-  __shared__ unsigned long long s_bound;
+  __shared__ NfView s_nv;  // near/far bound and bucket geometry (same in every block)
   Stats& st = s_st;
   if (tid == 0) {
     s_st = Stats{0, 0, 0, 0};
-    s_bound = kNoBound;
+    s_nv.bound = kNoBound;
+    s_nv.origin = 0;
+    s_nv.shift = 0;
+    s_nv.cursor = 0;
+    s_nv.cap = w.nf_cap;
+    s_nv.lists = w.nf_list;
+    s_nv.cnt = ctl->nf_cnt;
+    s_nv.beyond = &ctl->nf_beyond;
   }
   if ((p.crit & SSSP_POLICY_LEARNED) && p.policy) {  // (published by the first barrier below)
     float* pw = reinterpret_cast<float*>(smem + kPolicySmemOffset);
@@ -1513,38 +1911,47 @@ __device__ void solve_body(const SolveParams& p, const Grp& grp, unsigned char* 
   const bool dense_forced = (p.crit & SSSP_FRONTIER_DENSE) != 0;
   const uint32_t solo_cap = p.solo_max < kSoloCap ? p.solo_max : kSoloCap;
   unsigned int episodes = 0;
-  unsigned long long& bound = s_bound;  // near/far bound B (same in every block)
+  NfView& nv = s_nv;
   uint32_t nf_uses = 0;
   uint64_t k = 1;
   for (;;) {
-    uint32_t nF = ldcg_u32(&ctl->slot[k % 4].qcount);
+    PhaseHead h = load_head(ctl, k);
+    uint32_t nF = h.nQ;
     uint32_t nf_code = 0;
     if (k > (uint64_t)n + 1) {  // every phase settles a vertex: more phases mean a broken invariant
       if (leader) atomicCAS(&ctl->err, 0, (int)SSSP_ERR_INTERNAL);
       break;
     }
     if (md.nearfar) {
-      const uint32_t far = ldcg_u32(&ctl->far_count);
+      const uint32_t far = h.far;
       if (nF == 0 && far == 0) break;
-      const PhaseSlot* S0 = &ctl->slot[k % 4];
-      const unsigned long long T = md.use_out ? ldcg_u64(&S0->min_out) : ldcg_u64(&S0->min_d);
-      if (far > 0 && T > bound) {
-        if (!nf_refill(p, grp, md, k, sh, bound, nf_uses)) return;
-        nF = ldcg_u32(&ctl->slot[k % 4].qcount);
-        nf_code = kArmNfRefill;
-        if (nF == 0) {  // a refill always moves the vertex that attains T
+      const unsigned long long T = md.use_out ? h.min_out : h.min_d;
+      if (far > 0 && T > nv.bound) {
+        // raise B: from the bucket lists when they cover T, else by a full refill
+        bool full = nv.lists == nullptr;
+        if (!full && !nf_pull(p, grp, md, k, sh, nv, &full)) return;
+        if (full) {
+          if (!nf_refill(p, grp, md, k, sh, nv, nf_uses)) return;
+          nf_code = kArmNfRefill;
+        } else {
+          nf_code = kArmNfPull;
+        }
+        h = load_head(ctl, k);
+        nF = h.nQ;
+        if (nF == 0) {  // a refill or pull always moves the vertex that attains T
           if (leader) atomicCAS(&ctl->err, 0, (int)SSSP_ERR_INTERNAL);
           break;
         }
-      } else if (far == 0 && bound == kNoBound && (uint64_t)nF >= (uint64_t)p.nf_min * grp.size &&
+      } else if (far == 0 && nv.bound == kNoBound && (uint64_t)nF >= (uint64_t)p.nf_min * grp.size &&
                  (uint64_t)nF * 256 >= (uint64_t)p.nf_share * n) {
         // (with a policy too: while the fringe is split, every phase runs
         // the static sparse arm, see choose_arm)
-        if (!nf_split(p, grp, md, k, sh, bound, nf_uses)) return;
-        nF = ldcg_u32(&ctl->slot[k % 4].qcount);
-        if (bound != kNoBound) nf_code = kArmNfRefill;
+        if (!nf_split(p, grp, md, k, sh, nv, nf_uses)) return;
+        h = load_head(ctl, k);
+        nF = h.nQ;
+        if (nv.bound != kNoBound) nf_code = kArmNfRefill;
       }
-      if (bound != kNoBound) nf_code |= kArmNfActive;
+      if (nv.bound != kNoBound) nf_code |= kArmNfActive;
     } else if (nF == 0) {
       break;
     }
@@ -1556,15 +1963,16 @@ __device__ void solve_body(const SolveParams& p, const Grp& grp, unsigned char* 
       bool resume_relax = false;
       if (grp.rank == 0) {
         if (fast_solo) {
-          k = solo_episode(p, md, k, bound, nf_code, smem, st, grp.size > 1, &resume_relax);
+          k = solo_episode(p, md, k, nv, nf_code, smem, st, grp.size > 1, &resume_relax);
         } else {
           // three-step kind: the generic phase on this block alone
           const Grp solo{grp.bar, grp.err, grp.limit, 0, 1};
           while (nF != 0 && nF <= p.solo_max && k <= (uint64_t)n + 1) {
-            run_phase(p, solo, md, k, bound, 0u, sh, st);
+            run_phase(p, solo, md, k, nv, 0u, h, sh, st);
             ++k;
             if (tid == 0) ctl->heartbeat = k;
-            nF = ldcg_u32(&ctl->slot[k % 4].qcount);
+            h = load_head(ctl, k);
+            nF = h.nQ;
           }
         }
         if (grp.size > 1) {
@@ -1592,14 +2000,14 @@ __device__ void solve_body(const SolveParams& p, const Grp& grp, unsigned char* 
       ++episodes;
       if (resume_relax) {
         const Arm arm = arm_for(p, ldcg_u32(&ctl->slot[k % 4].qcount));
-        const bool ok = bound != kNoBound ? phase_relax<true>(p, grp, md, arm, k, bound, true, sh, st)
-                                          : phase_relax<false>(p, grp, md, arm, k, bound, true, sh, st);
+        const bool ok = nv.bound != kNoBound ? phase_relax<true>(p, grp, md, arm, k, nv, true, sh, st)
+                                             : phase_relax<false>(p, grp, md, arm, k, nv, true, sh, st);
         if (!ok) return;
         ++k;
       }
       continue;
     }
-    if (!run_phase(p, grp, md, k, bound, nf_code, sh, st)) return;
+    if (!run_phase(p, grp, md, k, nv, nf_code, h, sh, st)) return;
     ++k;
   }
   if (leader) {
@@ -1615,8 +2023,9 @@ __device__ void solve_body(const SolveParams& p, const Grp& grp, unsigned char* 
   }
 }
 
-__global__ void __launch_bounds__(kThreads) k_solve_grid(SolveParams p) {
+__global__ void __launch_bounds__(kThreads, 1) k_solve_grid(SolveParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
+  grid_sync_init();
   const Grp grp{&p.ws.ctl->bar, &p.ws.ctl->err, p.wait_ns, blockIdx.x, gridDim.x};
   solve_body(p, grp, smem);
 }
@@ -1649,6 +2058,7 @@ __global__ void __launch_bounds__(kThreads) k_solve_batch(const BatchItem* items
                                                            unsigned long long* phases_out, const float* policy) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned int s_item;
+  grid_sync_init();
   const unsigned int gidx = blockIdx.x / bpg, rank = blockIdx.x % bpg;
   GroupSlot* gs = &groups[gidx];
   const Grp grp{&gs->bar, err, wait_ns, rank, bpg};
@@ -1751,7 +2161,7 @@ sssp_status check_crit(const sssp_graph* g, uint32_t crit) {
 // co-resident blocks.
 int blocks_for(uint32_t n) {
   const int max_blocks = (int)resident_blocks();
-  const uint64_t want = grid_blocks() ? grid_blocks() : ((uint64_t)n + kTile - 1) / kTile;
+  const uint64_t want = grid_blocks() ? grid_blocks() : ((uint64_t)n + kVertsPerBlock - 1) / kVertsPerBlock;
   return (int)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)max_blocks));
 }
 
@@ -1772,6 +2182,7 @@ void workspace_free(Workspace* ws) {
   dev_free(ws->apx_in);
   dev_free(ws->apx_out);
   dev_free(ws->fresh);
+  dev_free(ws->nf_list);
   dev_free(ws->dist);
   dev_free(ws->ctl);
   cudaFreeHost(ws->ctl_host);
@@ -1783,9 +2194,11 @@ sssp_status workspace_alloc(uint32_t n, uint64_t m, bool want_cursors, bool want
   if (!ws) return fail(SSSP_ERR_OUT_OF_MEMORY, "host allocation failed");
   ws->n = n;
   sssp_status s = SSSP_OK;
+  ws->nf_cap = std::max<uint32_t>(n / 32, 1024u);
   if ((s = dev_alloc(&ws->vrec, n)) || (s = dev_alloc(&ws->status, n)) || (s = dev_alloc(&ws->q0, n)) ||
       (s = dev_alloc(&ws->q1, n)) || (s = dev_alloc(&ws->sp, n)) || (s = dev_alloc(&ws->ctl, 1)) ||
-      (s = dev_alloc(&ws->tile_owner, m / kTile + 2))) {
+      (s = dev_alloc(&ws->tile_owner, m / kTile + 2)) ||
+      (n <= kNearFarMaxVertices && (s = dev_alloc(&ws->nf_list, (size_t)kNfRing * ws->nf_cap)))) {
     workspace_free(ws);
     return s;
   }
@@ -1837,6 +2250,8 @@ SolveWS ws_view(Workspace* ws, unsigned long long* dist, uint32_t crit, bool has
   w.apx_in = apx ? ws->apx_in : nullptr;
   w.apx_out = apx ? ws->apx_out : nullptr;
   w.fresh = apx ? ws->fresh : nullptr;
+  w.nf_list = ws->nf_list;
+  w.nf_cap = ws->nf_list ? ws->nf_cap : 0;
   w.ctl = ws->ctl;
   return w;
 }
@@ -2082,7 +2497,7 @@ uint32_t choose_bpg(sssp_graph* const* graphs, uint32_t count) {
   uint64_t maxn = 0;
   for (uint32_t i = 0; i < count; ++i) maxn = std::max<uint64_t>(maxn, graphs[i]->n);
   const uint32_t bpg = std::max<uint32_t>(1, resident / std::max<uint32_t>(1, count));
-  const uint32_t useful = (uint32_t)std::max<uint64_t>(1, (maxn + kTile - 1) / kTile);
+  const uint32_t useful = (uint32_t)std::max<uint64_t>(1, (maxn + kVertsPerBlock - 1) / kVertsPerBlock);
   return std::min(bpg, useful);
 }
 

@@ -6,9 +6,16 @@
 namespace sssp {
 
 constexpr int kThreads = 512;
-constexpr int kRelaxItems = 2;
-constexpr int kSelItems = 2;  // fringe entries per thread per selection chunk
-constexpr int kTile = kThreads * kRelaxItems;
+constexpr int kWarps = kThreads / 32;
+// Grid phases are warp-centric: a warp takes a chunk of 32 * kSelItems fringe
+// entries in the selection step and a tile of kTile consecutive edges of the
+// relax list in the relax step, with all of a lane's loads in flight together
+// and no block barrier inside the loop.
+constexpr int kRelaxItems = 4;  // edges per lane per relax tile
+constexpr int kSelItems = 4;    // fringe entries per lane per selection chunk
+constexpr int kTile = 32 * kRelaxItems;
+// A single solve uses one block per this many vertices (at most all co-resident blocks).
+constexpr uint32_t kVertsPerBlock = 1024;
 // Solo mode (one block runs whole phases with its queues in shared memory):
 // fringe and relax list hold at most kSoloCap entries.
 constexpr uint32_t kSoloCap = 4096;
@@ -16,9 +23,9 @@ constexpr uint32_t kSoloMaxDefault = kSoloCap;     // fringe size limit
 constexpr uint32_t kSoloEdgesDefault = 2048;       // relax edges above which a solo phase hands off
 constexpr uint32_t kNearFarMinDefault = 8192;      // fringe size per block of the solve at which the near/far split starts
 constexpr uint32_t kNearFarShareDefault = 32;      // ... and fringe share of n, in 256ths
-constexpr size_t kGridSmem = 66 * sizeof(unsigned long long)                               // reduction scratch, bases
-                             + kTile * (2 * sizeof(uint32_t) + sizeof(unsigned long long))  // relax tile
-                             + 36 * sizeof(uint32_t);                                        // range, scan
+constexpr size_t kGridSmem = 66 * sizeof(unsigned long long)                                         // reduction scratch, bases
+                             + kWarps * kTile * (2 * sizeof(uint32_t) + sizeof(unsigned long long))  // relax tiles
+                             + 36 * sizeof(uint32_t);                                                  // range, scan
 constexpr size_t kSoloSmem = 64 * sizeof(unsigned long long)                       // reduction scratch
                              + 2 * kSoloCap * sizeof(uint32_t)                     // two queues
                              + kSoloCap * (2 * sizeof(uint32_t) + sizeof(unsigned long long))  // relax list
@@ -49,6 +56,6 @@ struct SolveParams {
 
 // One whole solve per cooperative launch (all blocks co-resident), kThreads
 // threads per block, kSmemBytes of dynamic shared memory.
-__global__ void __launch_bounds__(kThreads) k_solve_grid(SolveParams p);
+__global__ void __launch_bounds__(kThreads, 1) k_solve_grid(SolveParams p);
 
 }  // namespace sssp

@@ -121,6 +121,8 @@ struct Workspace {
   unsigned long long* apx_in;   // [n] APPROX values (allocated with the cursors)
   unsigned long long* apx_out;  // [n]
   uint32_t* fresh;              // [n]
+  uint32_t* nf_list;            // [kNfRing * nf_cap] far-vertex bucket lists
+  uint32_t nf_cap;
   unsigned long long* dist;  // used when the caller's distance buffer is host memory
   Ctl* ctl;
   Ctl* ctl_host;  // pinned mirror for read-back

@@ -185,7 +185,7 @@ extern "C" sssp_status sssp_solve_noalloc(uint32_t n, uint64_t m, const uint64_t
   p.nf_target = nearfar_target();
   p.nf_share = nearfar_share();
   p.policy = nullptr;
-  const uint64_t want = ((uint64_t)n + kTile - 1) / kTile;
+  const uint64_t want = ((uint64_t)n + kVertsPerBlock - 1) / kVertsPerBlock;
   const int grid = (int)(want < (uint64_t)blocks ? (want > 0 ? want : 1) : blocks);
   void* args[] = {&p};
   SSSP_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_solve_grid, dim3(grid), dim3(kThreads), args, kSmemBytes,

@@ -341,12 +341,14 @@ def test_batch_autotune_keeps_results():
 
 @pytest.mark.parametrize("crit", [sp.IN_OUT, sp.IN_STATIC, sp.OUT_STATIC], ids=["in_out", "in", "out"])
 def test_nearfar_split_runs_and_changes_nothing(crit):
-    """With a small split threshold the fringe is split and refilled many times
-    (trace arm bits 2 and 3); every per-phase figure still equals the oracle's."""
+    """With a small split threshold the fringe is split and its bound raised
+    many times (trace arm bits 2: split active, 3: full refill, 4: pull from the
+    far-vertex bucket lists); every per-phase figure still equals the oracle's."""
     g = gg.workload(1).graphs[0]
     G = sp.Graph.from_csr(g, reverse=True)
     ref = oracle.dijkstra(g, 0)
     sim = oracle.simulate(g, 0, crit, dist_ref=ref, trace=True)
+    refills = pulls = 0
     try:
         for tune in ["nearfar_grid_3blk", "nearfar_solo_3blk", "nearfar_auto_target"]:
             sp.set_tuning()
@@ -354,7 +356,9 @@ def test_nearfar_split_runs_and_changes_nothing(crit):
             check(g, G, 0, crit, ref)
             _, st, _, tr = sp.solve_trace(G, 0, crit, trace_cap=1 << 20)
             arm = tr["arm"].astype(np.uint32)
-            assert (arm & 4).any() and (arm & 8).sum() >= 2, tune
+            assert (arm & 4).any() and ((arm & 24) != 0).sum() >= 2, tune
+            refills += int(((arm & 8) != 0).sum())
+            pulls += int(((arm & 16) != 0).sum())
             q, f = tr["queued"], tr["frontier"]
             assert (q <= f).all() and (q[(arm & 4) == 0] == f[(arm & 4) == 0]).all()
             assert (q < f).any()  # some phases scanned only the near part
@@ -363,10 +367,11 @@ def test_nearfar_split_runs_and_changes_nothing(crit):
             assert (tr["min_d"] == sim.trace[:, 2]).all()  # thresholds exact after every refill
             if crit & sp.OUT_STATIC:
                 assert (tr["min_out"] == sim.trace[:, 3]).all()
+        assert refills >= 1 and pulls >= 1, (refills, pulls)  # both ways of raising B ran
         sp.set_tuning()
         sp.set_tuning(**TUNINGS["nearfar_grid_3blk"])
         _, _, _, tr = sp.solve_trace(G, 0, sp.SIMPLE, trace_cap=1 << 20)
-        assert not (tr["arm"].astype(np.uint32) & 12).any()  # dynamic IN: never split
+        assert not (tr["arm"].astype(np.uint32) & 28).any()  # dynamic IN: never split
     finally:
         sp.set_tuning()
 
