@@ -185,8 +185,12 @@ def _time(G, s, crit, reps=5):
 
 
 def test_trained_policy_gain(capsys):
-    """Train on small graphs of every family, evaluate on larger held-out ones:
-    the trained network's solve time against the fixed IN+OUT method."""
+    """Train on small graphs of every family, evaluate on larger held-out ones.
+    The judge is the fastest fixed policy: each of the network's four arms run
+    on its own for the whole solve.  In total over the held-out graphs the
+    trained network is no slower than the fixed IN+OUT method (2 % allowed for
+    timing noise) and within 10 % of choosing the fastest fixed arm per graph
+    in hindsight; on some graph it beats IN+OUT by at least 5 %."""
     from paper_1903_12085_gb300 import policy as pol
 
     w, hist = pol.fit_and_load()
@@ -201,14 +205,21 @@ def test_trained_policy_gain(capsys):
     for wl in held_out:
         gi, s = wl.solves[0]
         G = sp.Graph.from_csr(wl.graphs[gi], reverse=True)
-        t_fix, p_fix = _time(G, s, sp.IN_OUT)
+        arms = [_time(G, s, crit)[0] for crit in pol.ARMS]
         t_learn, p_learn = _time(G, s, sp.IN_OUT | sp.POLICY_LEARNED)
-        rows.append((wl.name, t_fix, p_fix, t_learn, p_learn))
+        rows.append((wl.name, arms, t_learn, p_learn))
     with capsys.disabled():
-        print("\npolicy gain (held-out graphs): name, IN+OUT ms, phases, learned ms, phases, speedup")
-        for r in rows:
-            print(f"  {r[0]:24s} {r[1]:9.3f} {r[2]:7d} {r[3]:9.3f} {r[4]:7d} {r[1] / r[3]:6.2f}x")
-    total_fix = sum(r[1] for r in rows)
-    total_learn = sum(r[3] for r in rows)
-    assert total_learn <= 1.10 * total_fix  # never much worse in total
-    assert max(r[1] / r[3] for r in rows) >= 1.05  # and a real gain on some held-out graph
+        print("\npolicy vs fixed arms (held-out graphs, ms): name, IN+OUT sparse/dense, IN-SIMPLE|OUT sparse/dense,"
+              " learned (phases), speedup vs IN+OUT, vs fastest arm")
+        for name, arms, tl, pl in rows:
+            print(f"  {name:24s} " + " ".join(f"{a:9.3f}" for a in arms) +
+                  f" {tl:9.3f} ({pl:6d}) {arms[0] / tl:5.2f}x {min(arms) / tl:5.2f}x")
+    total_learn = sum(r[2] for r in rows)
+    total_in_out = sum(r[1][0] for r in rows)
+    total_best = sum(min(r[1]) for r in rows)
+    with capsys.disabled():
+        print(f"  total: learned {total_learn:.3f} ms, IN+OUT {total_in_out:.3f} ms, "
+              f"fastest arm per graph {total_best:.3f} ms")
+    assert total_learn <= 1.02 * total_in_out
+    assert total_learn <= 1.10 * total_best
+    assert max(r[1][0] / r[2] for r in rows) >= 1.05
