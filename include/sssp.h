@@ -389,6 +389,15 @@ sssp_status sssp_device_memory_in_use(uint64_t* bytes);
  * returns.  Default 2e9.  Applies to launches made after the call. */
 sssp_status sssp_set_wait_limit_ns(uint64_t ns);
 
+/* Largest L2 fetch on a DRAM miss, in bytes (32, 64 or 128), for the CUDA
+ * context of the current device: cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity).
+ * The solves gather 16-byte vertex records at random, so a fetch larger than
+ * a 32-byte sector mostly moves bytes nobody reads; the setting lasts until
+ * the process exits or it is set again and applies to all work of the
+ * context, which is why the library never changes it by itself.  A library
+ * feature with no counterpart in the paper. */
+sssp_status sssp_set_l2_fetch_granularity(uint32_t bytes);
+
 /* Self-test of the bounded in-kernel wait that every grid barrier uses: one
  * thread waits on a device word that nothing writes, so the wait must run out
  * after limit_ns.  Returns SSSP_ERR_TIMEOUT (the expected outcome) and leaves

@@ -91,6 +91,7 @@ def lib():
             "sssp_batch_launch": [p, p],
             "sssp_batch_trace": [p, u32, p, u64, p, p],
             "sssp_set_wait_limit_ns": [u64],
+            "sssp_set_l2_fetch_granularity": [u32],
             "sssp_set_device_memory_limit": [u64],
             "sssp_device_memory_in_use": [p],
             "sssp_selftest_wait": [u64],
@@ -149,6 +150,12 @@ def version() -> str:
 
 def set_wait_limit_ns(ns: int):
     _check(lib().sssp_set_wait_limit_ns(int(ns)))
+
+
+def set_l2_fetch_granularity(nbytes: int):
+    """sssp_set_l2_fetch_granularity: 32, 64 or 128 bytes per L2 fetch on a
+    DRAM miss, for this process's CUDA context on the current device."""
+    _check(lib().sssp_set_l2_fetch_granularity(int(nbytes)))
 
 
 def set_device_memory_limit(nbytes: int):

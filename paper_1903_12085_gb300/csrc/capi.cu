@@ -135,6 +135,14 @@ extern "C" sssp_status sssp_set_wait_limit_ns(uint64_t ns) {
   return SSSP_OK;
 }
 
+extern "C" sssp_status sssp_set_l2_fetch_granularity(uint32_t bytes) {
+  sssp::clear_error();
+  if (bytes != 32 && bytes != 64 && bytes != 128)
+    return sssp::fail(SSSP_ERR_INVALID_ARG, "L2 fetch granularity must be 32, 64 or 128 bytes (got %u)", bytes);
+  SSSP_CUDA_TRY(cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, (size_t)bytes));
+  return SSSP_OK;
+}
+
 extern "C" const char* sssp_last_error(void) { return sssp::t_err; }
 
 extern "C" const char* sssp_version(void) { return "sssp-gb300 0.1 (sm_103a)"; }

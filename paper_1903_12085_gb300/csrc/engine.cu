@@ -206,7 +206,18 @@ struct Mode {
   uint32_t apx_k;    // its recomputation interval
   bool dijk;
   bool nearfar;      // the fringe may be split into a near queue and a far part
+  // Status bytes (U/F/S) are read only by dense scans, the dynamic and
+  // full/weak minima, APPROX and DIJK; with static criteria on the sparse queue
+  // nothing reads them, so settling and discovering a vertex write none.  A
+  // policy (its arms may scan densely or use IN-SIMPLE) needs them only until
+  // the fringe is split: from then on every phase runs its static sparse arm.
+  bool status;          // maintain the status bytes
+  bool status_presplit;  // ... only while the fringe is not split
 };
+
+__device__ __forceinline__ bool status_live(const Mode& md, bool split) {
+  return md.status && !(md.status_presplit && split);
+}
 
 // The near/far split needs static keys d(v) - inmin(v) (no IN-SIMPLE phase
 // while it is active: a policy is then limited to its IN-STATIC arms), fused
@@ -226,6 +237,10 @@ __device__ __forceinline__ Mode mode_of(const SolveParams& p) {
   const bool policy = (crit & SSSP_POLICY_LEARNED) != 0;
   m.use_in = (crit & (SSSP_IN_STATIC | SSSP_IN_SIMPLE | SSSP_IN_FULL)) != 0 || policy;
   m.nearfar = m.fused && !(crit & SSSP_IN_SIMPLE) && p.nf_min != 0 && p.g.n <= kNearFarMaxVertices;
+  const bool reads_status = (crit & (SSSP_FRONTIER_DENSE | SSSP_FRONTIER_AUTO | SSSP_IN_SIMPLE | SSSP_OUT_SIMPLE |
+                                     SSSP_IN_FULL | SSSP_OUT_WEAK | SSSP_APPROX | SSSP_DIJK)) != 0;
+  m.status = reads_status || policy;
+  m.status_presplit = policy && !reads_status;
   return m;
 }
 
@@ -462,7 +477,7 @@ __device__ __forceinline__ void relax_edge_rec(const SolveParams& p, const Mode&
     if (rt.d == kUnexplored) {
       old = atomicMin(&w.vrec[t].d, enc);
       if (old == kUnexplored) {
-        w.status[t] = kF;
+        if (status_live(md, kNF)) w.status[t] = kF;
         if (kNF && (enc & kFarBit)) {
           ++dfar;
           if (nv.lists) app = nf_bucket(nv, enc, rt.im);
@@ -525,11 +540,13 @@ struct PhaseHead {
   uint32_t nQ;
   uint32_t far;
   unsigned long long min_d, min_out;
+  bool split;  // near/far split active (from the block's own state)
 };
 
-__device__ __forceinline__ PhaseHead load_head(const Ctl* ctl, uint64_t k) {
+__device__ __forceinline__ PhaseHead load_head(const Ctl* ctl, uint64_t k, bool split) {
   const PhaseSlot* S0 = &ctl->slot[k % 4];
   PhaseHead h;
+  h.split = split;
   h.nQ = ldcg_u32(&S0->qcount);
   h.far = ldcg_u32(&ctl->far_count);
   h.min_d = min(ldcg_u64(&S0->min_d), ldcg_u64(&S0->a_min_d));
@@ -557,6 +574,7 @@ __device__ __noinline__ bool phase_select(const SolveParams& p, const Grp& grp, 
   PhaseSlot* S0 = &ctl->slot[k % 4];
   PhaseSlot* S1 = &ctl->slot[(k + 1) % 4];
   const uint32_t nF = h.nQ;
+  const bool wstat = status_live(md, h.split);
   const bool dense = arm.dense;
   const bool in_dyn = md.use_in && arm.in_simple && w.cur_in != nullptr;
   if (leader) {
@@ -743,7 +761,7 @@ __device__ __noinline__ bool phase_select(const SolveParams& p, const Grp& grp, 
       }
       if (!sel && md.dijk) sel = (v == amin);
       if (sel) {
-        w.status[v] = kS;
+        if (wstat) w.status[v] = kS;
         w.vrec[v].d = dv | kSettledBit;
         if (w.settle_phase) w.settle_phase[v] = (uint32_t)k;
         rd[j] = __ldg(&g.rowdeg[v]);
@@ -1210,7 +1228,7 @@ __device__ uint64_t solo_episode(const SolveParams& p, const Mode& md, uint64_t 
           if (!sel && md.use_out) sel = dv <= minOut;
           const uint32_t v = sq[i];
           if (sel) {
-            w.status[v] = kS;
+            if (status_live(md, kNF)) w.status[v] = kS;
             w.vrec[v].d = dv | kSettledBit;
             if (w.settle_phase) w.settle_phase[v] = (uint32_t)k;
             rdj[j] = __ldg(&g.rowdeg[v]);
@@ -1965,7 +1983,7 @@ __device__ void solve_body(const SolveParams& p, const Grp& grp, unsigned char* 
   uint32_t nf_uses = 0;
   uint64_t k = 1;
   for (;;) {
-    PhaseHead h = load_head(ctl, k);
+    PhaseHead h = load_head(ctl, k, nv.bound != kNoBound);
     uint32_t nF = h.nQ;
     uint32_t nf_code = 0;
     if (k > (uint64_t)n + 1) {  // every phase settles a vertex: more phases mean a broken invariant
@@ -1986,7 +2004,7 @@ __device__ void solve_body(const SolveParams& p, const Grp& grp, unsigned char* 
         } else {
           nf_code = kArmNfPull;
         }
-        h = load_head(ctl, k);
+        h = load_head(ctl, k, nv.bound != kNoBound);
         nF = h.nQ;
         if (nF == 0) {  // a refill or pull always moves the vertex that attains T
           if (leader) atomicCAS(&ctl->err, 0, (int)SSSP_ERR_INTERNAL);
@@ -1997,7 +2015,7 @@ __device__ void solve_body(const SolveParams& p, const Grp& grp, unsigned char* 
         // (with a policy too: while the fringe is split, every phase runs
         // the static sparse arm, see choose_arm)
         if (!nf_split(p, grp, md, k, sh, nv, nf_uses)) return;
-        h = load_head(ctl, k);
+        h = load_head(ctl, k, nv.bound != kNoBound);
         nF = h.nQ;
         if (nv.bound != kNoBound) nf_code = kArmNfRefill;
       }
@@ -2021,7 +2039,7 @@ __device__ void solve_body(const SolveParams& p, const Grp& grp, unsigned char* 
             run_phase(p, solo, md, k, nv, 0u, h, sh, st);
             ++k;
             if (tid == 0) ctl->heartbeat = k;
-            h = load_head(ctl, k);
+            h = load_head(ctl, k, nv.bound != kNoBound);
             nF = h.nQ;
           }
         }
