@@ -336,7 +336,7 @@ sssp_status sssp_solve_noalloc(uint32_t n, uint64_t m, const uint64_t* row_offse
                                uint64_t* dist_out, uint64_t* phases_out, void* stream);
 
 /* Execution tuning (results never depend on it).  solo_max_frontier: a
- * phase whose fringe has at most this many vertices (and at most 4096) runs on
+ * phase whose fringe has at most this many vertices (and at most 2048) runs on
  * a single block with its queues in shared memory (0 = never); if its relax
  * list then has more than solo_max_edges edges, the relax step is handed to
  * all blocks of the solve;
@@ -358,7 +358,7 @@ sssp_status sssp_solve_noalloc(uint32_t n, uint64_t m, const uint64_t* row_offse
  * nearfar_min_share: the split also needs a fringe of at least this many
  * 256ths of n (0 = no such condition).
  * Applies to launches made after the call; sssp_set_tuning(NULL) restores the
- * defaults (4096, 0, 0, 2048, 8192, 0, 32). */
+ * defaults (2048, 0, 0, 2048, 8192, 0, 32). */
 typedef struct {
   uint32_t solo_max_frontier;
   uint32_t batch_blocks_per_solve;

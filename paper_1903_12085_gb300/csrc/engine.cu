@@ -128,15 +128,27 @@ __device__ __forceinline__ uint32_t in_min_dynamic(const GraphView& g, const Sol
 
 // OUT-WEAK term of fringe vertex u on the phase-start state: the minimum over
 // out-edges (u,w) with w not settled of c(u,w) for w in F and c(u,w) +
-// outmin(w) for w unexplored (eq. crit:outweak).  A full scan of the row (the
-// term is not monotone: it drops when w enters F and grows when w settles).
+// outmin(w) for w unexplored (eq. crit:outweak).  The term is not monotone (it
+// drops when w enters F and grows when w settles), so it is recomputed in every
+// phase, but cheaply: the row is sorted by cost, every term of an edge is at
+// least its cost, so the scan stops at the first edge whose cost reaches the
+// best term found; and it starts at the out-cursor, which skips the row's
+// prefix of settled targets (S only grows, so the cursor only moves forward,
+// as in Proposition 3).  The caller is the only thread computing u's term in
+// the phase.
 __device__ __forceinline__ unsigned long long out_min_weak(const GraphView& g, const SolveWS& w, uint32_t u) {
-  const uint64_t b = __ldg(&g.row_off[u]), e = __ldg(&g.row_off[u + 1]);
+  const uint64_t e = __ldg(&g.row_off[u + 1]);
+  const uint64_t c0 = w.cur_out ? (uint64_t)ldcg_u32(&w.cur_out[u]) : __ldg(&g.row_off[u]);
+  uint64_t skip = c0;  // end of the settled prefix
   unsigned long long best = kInf64;
-  for (uint64_t c = b; c < e; ++c) {
+  for (uint64_t c = c0; c < e; ++c) {
     const uint2 ed = __ldg(&g.edges[c]);
+    if ((unsigned long long)ed.y >= best) break;  // no later edge can give a smaller term
     const uint8_t st = ldcg_u8(&w.status[ed.x]);
-    if (st == kS) continue;
+    if (st == kS) {
+      if (skip == c) skip = c + 1;
+      continue;
+    }
     unsigned long long x = ed.y;
     if (st == kU) {
       const uint32_t o = __ldg(&g.out_min[ed.x]);
@@ -145,6 +157,7 @@ __device__ __forceinline__ unsigned long long out_min_weak(const GraphView& g, c
     }
     best = x < best ? x : best;
   }
+  if (w.cur_out && skip != c0) w.cur_out[u] = (uint32_t)skip;
   return best;
 }
 
@@ -152,13 +165,20 @@ __device__ __forceinline__ unsigned long long out_min_weak(const GraphView& g, c
 // in-edges (w,v) with w not settled of c(w,v) for w in F and c(w,v) + inmin(w)
 // for w unexplored (eq. crit:in; an unexplored w has no settled in-neighbour,
 // so its static in-minimum is the one the criterion needs, Proposition 1).
+// Same scan as out_min_weak over the cost-sorted in-row, from the in-cursor.
 __device__ __forceinline__ unsigned long long in_min_full(const GraphView& g, const SolveWS& w, uint32_t v) {
-  const uint64_t b = __ldg(&g.rrow_off[v]), e = __ldg(&g.rrow_off[v + 1]);
+  const uint64_t e = __ldg(&g.rrow_off[v + 1]);
+  const uint64_t c0 = w.cur_in ? (uint64_t)ldcg_u32(&w.cur_in[v]) : __ldg(&g.rrow_off[v]);
+  uint64_t skip = c0;
   unsigned long long best = kInf64;
-  for (uint64_t c = b; c < e; ++c) {
+  for (uint64_t c = c0; c < e; ++c) {
     const uint2 ed = __ldg(&g.redges[c]);
+    if ((unsigned long long)ed.y >= best) break;
     const uint8_t st = ldcg_u8(&w.status[ed.x]);
-    if (st == kS) continue;
+    if (st == kS) {
+      if (skip == c) skip = c + 1;
+      continue;
+    }
     unsigned long long x = ed.y;
     if (st == kU) {
       const uint32_t i = __ldg(&g.in_min[ed.x]);
@@ -167,6 +187,7 @@ __device__ __forceinline__ unsigned long long in_min_full(const GraphView& g, co
     }
     best = x < best ? x : best;
   }
+  if (w.cur_in && skip != c0) w.cur_in[v] = (uint32_t)skip;
   return best;
 }
 
@@ -1132,14 +1153,19 @@ __device__ uint64_t solo_episode(const SolveParams& p, const Mode& md, uint64_t 
   unsigned long long* sp_d = reinterpret_cast<unsigned long long*>(sqb + kSoloCap);
   uint32_t* sp_row = reinterpret_cast<uint32_t*>(sp_d + kSoloCap);
   uint32_t* sp_base = sp_row + kSoloCap;
-  // records of this phase's fringe entries, staged by queue position
+  // records of this phase's fringe entries, staged by queue position; thread t
+  // stages entries t, t + blockDim, ... and is also the thread that decides
+  // them, so staging needs no block barrier
   unsigned long long* r_d = reinterpret_cast<unsigned long long*>(sp_base + kSoloCap);
   uint32_t* r_im = reinterpret_cast<uint32_t*>(r_d + kSoloCap);
   uint32_t* r_om = r_im + kSoloCap;
-  __shared__ unsigned int s_qn, s_settled;
-  __shared__ unsigned int s_wk[32], s_wr[32], s_we[32];  // per-warp counts, then offsets
-  __shared__ unsigned long long s_relax, s_thr_d, s_thr_o;
-  __shared__ int s_dfar;
+  // per-phase counters, double-buffered by phase parity: the buffer of phase
+  // k + 1 is cleared during phase k, after every thread has read it as phase
+  // k - 1's
+  __shared__ unsigned int s_qn[2], s_settled[2];
+  __shared__ unsigned int s_wk[32], s_wr[32], s_we[32];  // per-warp counts
+  __shared__ unsigned long long s_relax[2], s_thr_d[2], s_thr_o[2];
+  __shared__ int s_dfar[2];
   *handoff = false;
 
   const uint32_t cap = p.solo_max < kSoloCap ? p.solo_max : kSoloCap;
@@ -1160,7 +1186,16 @@ __device__ uint64_t solo_episode(const SolveParams& p, const Mode& md, uint64_t 
     uint32_t* sq = ((k - 1) & 1) ? sqb : sqa;
     for (uint32_t i = tid; i < nF; i += nthr) sq[i] = ldcg_u32(gq + i);
   }
+  if (tid < 2) {
+    s_qn[tid] = 0;
+    s_settled[tid] = 0;
+    s_relax[tid] = 0;
+    s_thr_d[tid] = s_thr_o[tid] = kInf64;
+    s_dfar[tid] = 0;
+  }
+  __syncthreads();
   for (;;) {
+    const int pb = (int)(k & 1);  // this phase's counter buffer
     const int cur = (int)((k - 1) & 1);
     const uint32_t* sq = cur ? sqb : sqa;
     uint32_t* sqn = cur ? sqa : sqb;
@@ -1172,14 +1207,7 @@ __device__ uint64_t solo_episode(const SolveParams& p, const Mode& md, uint64_t 
     const bool in_dyn = md.use_in && arm.in_simple && w.cur_in != nullptr;
     const uint32_t fs = nF + far;  // |F| at the start of the phase
     unsigned long long t0 = 0, t_sel = 0;
-    if (tid == 0) {
-      if (w.trace) t0 = globaltimer_ns();
-      s_qn = 0;
-      s_settled = 0;
-      s_relax = 0;
-      s_thr_d = s_thr_o = kInf64;
-      s_dfar = 0;
-    }
+    if (tid == 0 && w.trace) t0 = globaltimer_ns();
     // ---- B1: stage the fringe's records (all of a thread's loads in flight at once)
     for (uint32_t i0 = tid; i0 < nF; i0 += 4 * nthr) {
       VRec r[4];
@@ -1201,7 +1229,8 @@ __device__ uint64_t solo_episode(const SolveParams& p, const Mode& md, uint64_t 
         }
       }
     }
-    __syncthreads();
+    // IN-SIMPLE minima read status bytes that the selection below writes
+    if (in_dyn) __syncthreads();
     // ---- B2: select.  Pass 1 decides and issues the row loads of the settled
     // vertices; one block scan of per-warp counts gives every warp its output
     // offsets; pass 2 writes the kept entries and the relax list (no shared
@@ -1259,32 +1288,34 @@ __device__ uint64_t solo_episode(const SolveParams& p, const Mode& md, uint64_t 
       s_wk[warp] = wk;
       s_wr[warp] = wr;
       s_we[warp] = we;
-      if (ws) atomicAdd(&s_settled, ws);
+      if (ws) atomicAdd(&s_settled[pb], ws);
     }
     pd = warp_min_u64(pd);
     po = warp_min_u64(po);
     if (lane == 0) {
-      if (pd != kInf64) atomicMin(&s_thr_d, pd);
-      if (po != kInf64 && md.use_out) atomicMin(&s_thr_o, po);
+      if (pd != kInf64) atomicMin(&s_thr_d[pb], pd);
+      if (po != kInf64 && md.use_out) atomicMin(&s_thr_o[pb], po);
     }
     __syncthreads();
-    if (warp == 0) {  // exclusive scan of the per-warp counts
+    if (tid == 0) {  // the next phase's counters (every thread has read them as the last phase's)
+      s_qn[pb ^ 1] = 0;
+      s_settled[pb ^ 1] = 0;
+      s_relax[pb ^ 1] = 0;
+      s_thr_d[pb ^ 1] = s_thr_o[pb ^ 1] = kInf64;
+      s_dfar[pb ^ 1] = 0;
+    }
+    {
+      // every warp scans the per-warp counts itself: its offsets and the totals
       const unsigned int nw = nthr >> 5;
       const uint32_t a = lane < nw ? s_wk[lane] : 0, b = lane < nw ? s_wr[lane] : 0, c = lane < nw ? s_we[lane] : 0;
       const uint32_t ia = warp_inclusive_scan(a), ib = warp_inclusive_scan(b), ic = warp_inclusive_scan(c);
-      if (lane < nw) {
-        s_wk[lane] = ia - a;
-        s_wr[lane] = ib - b;
-        s_we[lane] = ic - c;
+      uint32_t koff = __shfl_sync(0xFFFFFFFFu, ia - a, warp);
+      uint32_t roff = __shfl_sync(0xFFFFFFFFu, ib - b, warp);
+      uint32_t eoff = __shfl_sync(0xFFFFFFFFu, ic - c, warp);
+      if (warp == 0 && lane == 31) {
+        s_qn[pb] = ia;
+        s_relax[pb] = ((unsigned long long)ib << 32) | ic;
       }
-      if (lane == 31) {
-        s_qn = ia;
-        s_relax = ((unsigned long long)ib << 32) | ic;
-      }
-    }
-    __syncthreads();
-    {
-      uint32_t koff = s_wk[warp], roff = s_wr[warp], eoff = s_we[warp];
       const unsigned int lt = (1u << lane) - 1u;
 #pragma unroll
       for (int j = 0; j < kIt; ++j) {
@@ -1315,7 +1346,7 @@ __device__ uint64_t solo_episode(const SolveParams& p, const Mode& md, uint64_t 
       }
     }
     __syncthreads();
-    const unsigned long long packed = s_relax;
+    const unsigned long long packed = s_relax[pb];
     const uint32_t nS = (uint32_t)(packed >> 32), E = (uint32_t)packed;
     if (can_handoff && E > p.solo_edges) {
       // state of a grid selection step of phase k, in global memory
@@ -1324,7 +1355,7 @@ __device__ uint64_t solo_episode(const SolveParams& p, const Mode& md, uint64_t 
             make_ulonglong2(sp_d[j], (unsigned long long)sp_row[j] | ((unsigned long long)sp_base[j] << 32));
         if (w.tile_owner) mark_tile_owner(w.tile_owner, j, sp_base[j], (j + 1 < nS ? sp_base[j + 1] : E) - sp_base[j]);
       }
-      const uint32_t kept = s_qn;
+      const uint32_t kept = s_qn[pb];
       const uint32_t nk = kept < kSoloCap ? kept : kSoloCap;
       for (uint32_t j = tid; j < nk; j += nthr) gqn[j] = sqn[j];
       if (tid == 0) {
@@ -1340,13 +1371,13 @@ __device__ uint64_t solo_episode(const SolveParams& p, const Mode& md, uint64_t 
         S0->min_d = minD;
         S0->min_out = minOut;
         S0->relax_packed = packed;
-        S0->settled_now = s_settled;
+        S0->settled_now = s_settled[pb];
         S0->arm = arm_code(arm, true) | nf_code;
         S0->t_start = t0;
         S0->t_select = globaltimer_ns();
         S1->qcount = kept;
-        S1->min_d = s_thr_d;
-        S1->min_out = s_thr_o;
+        S1->min_d = s_thr_d[pb];
+        S1->min_out = s_thr_o[pb];
         st_shared = st;
       }
       __threadfence();
@@ -1359,29 +1390,30 @@ __device__ uint64_t solo_episode(const SolveParams& p, const Mode& md, uint64_t 
     pd = kInf64;
     po = kInf64;
     int dfar = 0;
-    const SoloRelax sr{sp_d, sp_row, sp_base, nS, E, sqn, gqn, &s_qn};
+    const SoloRelax sr{sp_d, sp_row, sp_base, nS, E, sqn, gqn, &s_qn[pb]};
     if (kNF) solo_relax<true>(p, md, sr, nv, pd, po, dfar);
     else solo_relax<false>(p, md, sr, nv, pd, po, dfar);
     pd = warp_min_u64(pd);
     po = warp_min_u64(po);
     if (kNF) dfar = __reduce_add_sync(0xFFFFFFFFu, dfar);
     if (lane == 0) {
-      if (pd != kInf64) atomicMin(&s_thr_d, pd);
-      if (po != kInf64 && md.use_out) atomicMin(&s_thr_o, po);
-      if (dfar) atomicAdd(&s_dfar, dfar);
+      if (pd != kInf64) atomicMin(&s_thr_d[pb], pd);
+      if (po != kInf64 && md.use_out) atomicMin(&s_thr_o[pb], po);
+      if (dfar) atomicAdd(&s_dfar[pb], dfar);
     }
     __syncthreads();
-    const uint32_t nFn = s_qn;
+    const uint32_t nFn = s_qn[pb];
+    const uint32_t settled_now = s_settled[pb];
     if (tid == 0) {
       st.phases = k;
       st.sum_f += fs;
-      st.settled += s_settled;
+      st.settled += settled_now;
       st.relaxed += E;
       ctl->heartbeat = k;
       if (w.trace && k <= w.trace_cap) {
         sssp_phase_record r;
         r.frontier = fs;
-        r.settled = s_settled;
+        r.settled = settled_now;
         r.min_d = minD;
         r.min_out = md.use_out ? minOut : kInf64;
         r.deg_settled = E;
@@ -1397,15 +1429,14 @@ __device__ uint64_t solo_episode(const SolveParams& p, const Mode& md, uint64_t 
       }
     }
     nf_code &= ~(kArmNfRefill | kArmNfPull);  // a refill, pull or split only runs before the episode
-    minD = s_thr_d;
-    minOut = s_thr_o;
+    minD = s_thr_d[pb];
+    minOut = s_thr_o[pb];
     e_prev = E;
-    s_prev = s_settled;
+    s_prev = settled_now;
     f_prev = fs;
     nF = nFn;
-    if (kNF) far += (uint32_t)s_dfar;
+    if (kNF) far += (uint32_t)s_dfar[pb];
     ++k;
-    __syncthreads();  // shared counters are read before the next phase resets them
     if (nF == 0 || nF > cap || k > (uint64_t)n + 1) break;
     // thresholds above the bound are exact only after the far part is scanned
     if (kNF && far > 0 && (md.use_out ? minOut : minD) > nv.bound) break;
@@ -2309,8 +2340,9 @@ SolveWS ws_view(Workspace* ws, unsigned long long* dist, uint32_t crit, bool has
   w.q[1] = ws->q1;
   w.sp = ws->sp;
   w.dist = dist ? dist : ws->dist;
-  w.cur_out = (crit & SSSP_OUT_SIMPLE) ? ws->cur_out : nullptr;
-  w.cur_in = ((crit & (SSSP_IN_SIMPLE | SSSP_POLICY_LEARNED)) && has_reverse) ? ws->cur_in : nullptr;
+  w.cur_out = (crit & (SSSP_OUT_SIMPLE | SSSP_OUT_WEAK | SSSP_APPROX)) ? ws->cur_out : nullptr;
+  w.cur_in = ((crit & (SSSP_IN_SIMPLE | SSSP_IN_FULL | SSSP_APPROX | SSSP_POLICY_LEARNED)) && has_reverse)
+                 ? ws->cur_in : nullptr;
   w.im_dyn = w.cur_in ? ws->im_dyn : nullptr;
   w.tile_owner = ws->tile_owner;
   w.im_full = ((crit & SSSP_IN_FULL) && has_reverse) ? ws->im_full : nullptr;

@@ -18,7 +18,7 @@ constexpr int kTile = 32 * kRelaxItems;
 constexpr uint32_t kVertsPerBlock = 1024;
 // Solo mode (one block runs whole phases with its queues in shared memory):
 // fringe and relax list hold at most kSoloCap entries.
-constexpr uint32_t kSoloCap = 4096;
+constexpr uint32_t kSoloCap = 2048;
 constexpr uint32_t kSoloMaxDefault = kSoloCap;     // fringe size limit
 constexpr uint32_t kSoloEdgesDefault = 2048;       // relax edges above which a solo phase hands off
 constexpr uint32_t kNearFarMinDefault = 8192;      // fringe size per block of the solve at which the near/far split starts
