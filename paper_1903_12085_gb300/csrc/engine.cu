@@ -1153,12 +1153,9 @@ __device__ uint64_t solo_episode(const SolveParams& p, const Mode& md, uint64_t 
   unsigned long long* sp_d = reinterpret_cast<unsigned long long*>(sqb + kSoloCap);
   uint32_t* sp_row = reinterpret_cast<uint32_t*>(sp_d + kSoloCap);
   uint32_t* sp_base = sp_row + kSoloCap;
-  // records of this phase's fringe entries, staged by queue position; thread t
-  // stages entries t, t + blockDim, ... and is also the thread that decides
-  // them, so staging needs no block barrier
-  unsigned long long* r_d = reinterpret_cast<unsigned long long*>(sp_base + kSoloCap);
-  uint32_t* r_im = reinterpret_cast<uint32_t*>(r_d + kSoloCap);
-  uint32_t* r_om = r_im + kSoloCap;
+  // (thread t loads the records of fringe entries t, t + blockDim, ... into
+  // registers and decides those same entries: no block barrier between)
+  static_assert(kSoloCap % kThreads == 0, "solo entries per thread");
   // per-phase counters, double-buffered by phase parity: the buffer of phase
   // k + 1 is cleared during phase k, after every thread has read it as phase
   // k - 1's
@@ -1208,25 +1205,19 @@ __device__ uint64_t solo_episode(const SolveParams& p, const Mode& md, uint64_t 
     const uint32_t fs = nF + far;  // |F| at the start of the phase
     unsigned long long t0 = 0, t_sel = 0;
     if (tid == 0 && w.trace) t0 = globaltimer_ns();
-    // ---- B1: stage the fringe's records (all of a thread's loads in flight at once)
-    for (uint32_t i0 = tid; i0 < nF; i0 += 4 * nthr) {
-      VRec r[4];
+    // ---- B1: load the records of this thread's fringe entries (all in flight at once)
+    constexpr int kIt = kSoloCap / kThreads;
+    VRec r[kIt];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const uint32_t i = i0 + j * nthr;
-        if (i < nF) {
-          const uint32_t v = sq[i];
-          r[j] = ldcg_vrec(&w.vrec[v]);
-        }
-      }
+    for (int j = 0; j < kIt; ++j) {
+      const uint32_t i = tid + j * nthr;
+      if (i < nF) r[j] = ldcg_vrec(&w.vrec[sq[i]]);
+    }
+    if (in_dyn) {
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const uint32_t i = i0 + j * nthr;
-        if (i < nF) {
-          r_d[i] = r[j].d;
-          r_im[i] = in_dyn ? in_min_dynamic(g, w, sq[i], false) : r[j].im;
-          r_om[i] = r[j].om;
-        }
+      for (int j = 0; j < kIt; ++j) {
+        const uint32_t i = tid + j * nthr;
+        if (i < nF) r[j].im = in_min_dynamic(g, w, sq[i], false);
       }
     }
     // IN-SIMPLE minima read status bytes that the selection below writes
@@ -1235,7 +1226,6 @@ __device__ uint64_t solo_episode(const SolveParams& p, const Mode& md, uint64_t 
     // vertices; one block scan of per-warp counts gives every warp its output
     // offsets; pass 2 writes the kept entries and the relax list (no shared
     // atomics on the hot counters).
-    constexpr int kIt = kSoloCap / kThreads;
     unsigned long long pd = kInf64, po = kInf64;
     uint32_t selm[kIt], keepm[kIt];
     uint2 rdj[kIt];
@@ -1249,9 +1239,9 @@ __device__ uint64_t solo_episode(const SolveParams& p, const Mode& md, uint64_t 
         const bool valid = i < nF;
         bool sel = false;
         if (valid) {
-          const unsigned long long dv = r_d[i];
+          const unsigned long long dv = r[j].d;
           if (md.use_in) {
-            const uint32_t im = r_im[i];
+            const uint32_t im = r[j].im;
             sel = (im == kInf32) || dv <= minD + im;
           }
           if (!sel && md.use_out) sel = dv <= minOut;
@@ -1263,7 +1253,7 @@ __device__ uint64_t solo_episode(const SolveParams& p, const Mode& md, uint64_t 
             rdj[j] = __ldg(&g.rowdeg[v]);
           } else {
             pd = dv < pd ? dv : pd;
-            const uint32_t om = r_om[i];
+            const uint32_t om = r[j].om;
             if (om != kInf32) {
               const unsigned long long x = dv + om;
               po = x < po ? x : po;
@@ -1336,7 +1326,7 @@ __device__ uint64_t solo_episode(const SolveParams& p, const Mode& md, uint64_t 
           const uint32_t incl = warp_inclusive_scan(c);
           if (rl) {
             const uint32_t slot = roff + __popc(rm & lt);  // < |S'| <= nF <= kSoloCap
-            sp_d[slot] = r_d[i];
+            sp_d[slot] = r[j].d;
             sp_row[slot] = rdj[j].x;
             sp_base[slot] = eoff + incl - c;
           }

@@ -30,7 +30,6 @@ constexpr size_t kGridSmem = 66 * sizeof(unsigned long long)                    
 constexpr size_t kSoloSmem = 64 * sizeof(unsigned long long)                       // reduction scratch
                              + 2 * kSoloCap * sizeof(uint32_t)                     // two queues
                              + kSoloCap * (2 * sizeof(uint32_t) + sizeof(unsigned long long))  // relax list
-                             + kSoloCap * (sizeof(unsigned long long) + 2 * sizeof(uint32_t))  // staged records
                              + 16;
 // Graphs whose edges and vertex records take at most this many bytes are
 // prefetched into L2 when a solve starts (L2 holds 126 MiB).
