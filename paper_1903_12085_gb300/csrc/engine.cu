@@ -1061,14 +1061,35 @@ __device__ __noinline__ bool phase_relax(const SolveParams& p, const Grp& grp, c
   return true;
 }
 
+// The policy's last choice in grid mode and the phase it was made in (per
+// block; s_arm_k = ~0 at the start of every solve, see solve_body).
+static __shared__ Arm s_arm_last;
+static __shared__ unsigned long long s_arm_k;
+
 __device__ __forceinline__ bool run_phase(const SolveParams& p, const Grp& grp, const Mode& md, uint64_t k,
                                           const NfView& nv, uint32_t nf_code, const PhaseHead& h, const Shared& sh,
                                           Stats& st) {
   Arm arm;
-  if ((p.crit & SSSP_POLICY_LEARNED) && p.policy != nullptr) {  // (the previous phase's counts are its features)
-    const PhaseSlot* prev = &p.ws.ctl->slot[(k + 3) % 4];
-    arm = choose_arm(p, k, h.nQ, h.nQ + (md.nearfar ? h.far : 0u), (uint32_t)ldcg_u64(&prev->relax_packed),
-                     ldcg_u32(&prev->settled_now), ldcg_u32(&prev->fsize), nv.bound != kNoBound);
+  if ((p.crit & SSSP_POLICY_LEARNED) && p.policy != nullptr) {
+    // The network is evaluated in the first grid phase of a solve and then at
+    // most every 4th phase (its forward pass sits on the phase's critical
+    // path); the phases in between keep its last choice.  (The previous
+    // phase's counts are its features.)  Every block evaluates the same inputs.
+    if (nv.bound != kNoBound) {
+      arm = choose_arm(p, k, h.nQ, 0, 0, 0, 0, true);  // split: the static sparse arm
+    } else if (k <= s_arm_k || k - s_arm_k >= 4) {
+      const PhaseSlot* prev = &p.ws.ctl->slot[(k + 3) % 4];
+      arm = choose_arm(p, k, h.nQ, h.nQ + (md.nearfar ? h.far : 0u), (uint32_t)ldcg_u64(&prev->relax_packed),
+                       ldcg_u32(&prev->settled_now), ldcg_u32(&prev->fsize), false);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        s_arm_last = arm;
+        s_arm_k = k;
+      }
+      __syncthreads();
+    } else {
+      arm = s_arm_last;
+    }
   } else {
     arm = arm_for(p, h.nQ);
   }
@@ -1943,6 +1964,7 @@ __device__ void solve_body(const SolveParams& p, const Grp& grp, unsigned char* 
   Stats& st = s_st;
   if (tid == 0) {
     s_st = Stats{0, 0, 0, 0};
+    s_arm_k = ~0ull;
     s_nv.bound = kNoBound;
     s_nv.origin = 0;
     s_nv.shift = 0;
