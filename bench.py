@@ -80,7 +80,8 @@ def parse():
 # workload name and criterion, with a hash of the engine sources the capture ran
 # on: once the kernel changes the figure no longer applies and is reported null.
 MEASURED_TRAFFIC = {
-    ("grid_1024x1024", "in_out", "k_solve_grid"): (52220672 + 7912192, "9afd8ba9ec29eacd"),
+    # profiles/dram_batch_gnm2p24.md: one timed launch of the default step
+    ("gnm_n16777216_m268435456", "learned", "k_solve_batch"): (540043015000 + 44005125000, "5be595756701fa55"),
 }
 ENGINE_SOURCES = ("engine.cu", "engine.h", "common.cuh", "policy.cuh")
 
@@ -437,10 +438,13 @@ def main():
     achieved = alg_bytes / (step_avg_ms * 1e-3) / 1e9
     edge_only = 16 * per["edges_relaxed"] / (step_avg_ms * 1e-3) / 1e9
     kernel = "k_solve_batch" if batched else "k_solve_grid"
+    traffic = measured_traffic(wl.name, args.criterion, kernel)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": measured_traffic(wl.name, args.criterion, kernel), "peak_kind": peak_kind,
+                "traffic": traffic, "peak_kind": peak_kind,
                 "kernel": kernel, "launches_per_step": head.launches(),
-                "alg_bytes_per_step": alg_bytes, "edge_only_frac": edge_only / hbm}
+                "alg_bytes_per_step": alg_bytes, "edge_only_frac": edge_only / hbm,
+                # DRAM bytes the launch really moved (ncu) over the same step time
+                "dram_frac": None if traffic is None else traffic / (step_avg_ms * 1e-3) / 1e9 / hbm}
     if learned:
         train["arms_used"] = "per-phase choice logged in the trace records"
 
