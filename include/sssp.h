@@ -358,7 +358,7 @@ sssp_status sssp_solve_noalloc(uint32_t n, uint64_t m, const uint64_t* row_offse
  * nearfar_min_share: the split also needs a fringe of at least this many
  * 256ths of n (0 = no such condition).
  * Applies to launches made after the call; sssp_set_tuning(NULL) restores the
- * defaults (2048, 0, 0, 2048, 8192, 0, 32). */
+ * defaults (2048, 0, 0, 2048, 8192, 0, 8). */
 typedef struct {
   uint32_t solo_max_frontier;
   uint32_t batch_blocks_per_solve;

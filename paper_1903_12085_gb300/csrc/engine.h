@@ -22,7 +22,7 @@ constexpr uint32_t kSoloCap = 2048;
 constexpr uint32_t kSoloMaxDefault = kSoloCap;     // fringe size limit
 constexpr uint32_t kSoloEdgesDefault = 2048;       // relax edges above which a solo phase hands off
 constexpr uint32_t kNearFarMinDefault = 8192;      // fringe size per block of the solve at which the near/far split starts
-constexpr uint32_t kNearFarShareDefault = 32;      // ... and fringe share of n, in 256ths
+constexpr uint32_t kNearFarShareDefault = 8;       // ... and fringe share of n, in 256ths
 constexpr size_t kGridSmem = 66 * sizeof(unsigned long long)                                         // reduction scratch, bases
                              + kWarps * kTile * (2 * sizeof(uint32_t) + sizeof(unsigned long long))  // relax tiles
                              + 36 * sizeof(uint32_t)                                                   // range, scan
