@@ -1159,9 +1159,10 @@ __device__ __forceinline__ void solo_relax(const SolveParams& p, const Mode& md,
 // slot[k%3].  Exit at phase k: the same state with slot[(k+1)%3] reset (no
 // handoff), or the state after a grid selection step of phase k (handoff).
 // All threads of the block call it.
-__device__ uint64_t solo_episode(const SolveParams& p, const Mode& md, uint64_t k, const NfView& nv,
+__device__ __forceinline__ uint64_t solo_episode(const SolveParams& p, const Mode& md_shared, uint64_t k, const NfView& nv,
                                  uint32_t nf_code, unsigned char* smem, Stats& st_shared, bool can_handoff,
                                  bool* handoff) {
+  const Mode md = md_shared;  // in registers for the episode (read in every step)
   const GraphView& g = p.g;
   const SolveWS& w = p.ws;
   Ctl* ctl = w.ctl;
@@ -1945,17 +1946,33 @@ __device__ __noinline__ bool nf_pull(const SolveParams& p, const Grp& grp, const
 
 // Initialise, run all phases (switching to solo mode while the fringe is
 // small), write the distances.  Every block of the group calls it.
-__device__ void solve_body(const SolveParams& p, const Grp& grp, unsigned char* smem) {
+// `p` is the block's shared copy of the parameters (what the out-of-line
+// phase steps take); `pk` is the same parameters where the inlined solo
+// episodes read them fastest (the kernel parameter bank of a single solve).
+__device__ void solve_body(const SolveParams& p, const SolveParams& pk, const Grp& grp_in, unsigned char* smem) {
   const GraphView& g = p.g;
   const SolveWS& w = p.ws;
   Ctl* ctl = w.ctl;
   const uint32_t n = g.n;
   const unsigned int tid = threadIdx.x, nthr = blockDim.x;
+  // The group, the shared-memory layout and the mode are the same for every
+  // thread of the block: one copy in shared memory, which the steps read
+  // through references (per-thread copies would live in local memory).
+  __shared__ Grp s_grp;
+  __shared__ Shared s_sh;
+  __shared__ Mode s_md;
+  if (tid == 0) {
+    s_grp = grp_in;
+    s_sh = carve(smem);
+    s_md = mode_of(p);
+  }
+  __syncthreads();
+  const Grp& grp = s_grp;
+  const Shared& sh = s_sh;
+  const Mode& md = s_md;
   const uint64_t gthreads = (uint64_t)grp.size * nthr;
   const uint64_t gtid = (uint64_t)grp.rank * nthr + tid;
   const bool leader = grp.rank == 0 && tid == 0;
-  const Shared sh = carve(smem);
-  const Mode md = mode_of(p);
   // Counters and the near/far bound live in shared memory: they are touched
   // once per phase at most, and keeping them out of registers leaves the
   // phase loops more room.
@@ -2074,7 +2091,7 @@ __device__ void solve_body(const SolveParams& p, const Grp& grp, unsigned char* 
       bool resume_relax = false;
       if (grp.rank == 0) {
         if (fast_solo) {
-          k = solo_episode(p, md, k, nv, nf_code, smem, st, grp.size > 1, &resume_relax);
+          k = solo_episode(pk, md, k, nv, nf_code, smem, st, grp.size > 1, &resume_relax);
         } else {
           // three-step kind: the generic phase on this block alone
           const Grp solo{grp.bar, grp.err, grp.limit, 0, 1};
@@ -2134,11 +2151,17 @@ __device__ void solve_body(const SolveParams& p, const Grp& grp, unsigned char* 
   }
 }
 
+// The solve's parameters live in shared memory, one copy per block: every
+// step reads them through a reference, and a per-thread copy in local memory
+// would take L1 space (and L2 traffic) from the graph's data.
 __global__ void __launch_bounds__(kThreads, 1) k_solve_grid(SolveParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ SolveParams s_p;
   grid_sync_init();
-  const Grp grp{&p.ws.ctl->bar, &p.ws.ctl->err, p.wait_ns, blockIdx.x, gridDim.x};
-  solve_body(p, grp, smem);
+  if (threadIdx.x == 0) s_p = p;
+  __syncthreads();
+  const Grp grp{&s_p.ws.ctl->bar, &s_p.ws.ctl->err, s_p.wait_ns, blockIdx.x, gridDim.x};
+  solve_body(s_p, p, grp, smem);
 }
 
 // Batched solver: the grid is split into groups of `bpg` blocks; the first
@@ -2181,19 +2204,22 @@ __global__ void __launch_bounds__(kThreads) k_solve_batch(const BatchItem* items
     const unsigned int it = s_item;
     if (!grp.sync()) return;  // everyone has read the mailbox before it is reused
     if (it >= count) break;
-    SolveParams p;
-    p.g = items[it].g;
-    p.ws = items[it].ws;
-    p.source = items[it].source;
-    p.crit = crit;
-    p.wait_ns = wait_ns;
-    p.solo_max = tu.solo_max;
-    p.solo_edges = tu.solo_edges;
-    p.nf_min = tu.nf_min;
-    p.nf_target = tu.nf_target;
-    p.nf_share = tu.nf_share;
-    p.policy = policy;
-    solve_body(p, grp, smem);
+    __shared__ SolveParams p;  // one copy per block (see k_solve_grid)
+    if (threadIdx.x == 0) {
+      p.g = items[it].g;
+      p.ws = items[it].ws;
+      p.source = items[it].source;
+      p.crit = crit;
+      p.wait_ns = wait_ns;
+      p.solo_max = tu.solo_max;
+      p.solo_edges = tu.solo_edges;
+      p.nf_min = tu.nf_min;
+      p.nf_target = tu.nf_target;
+      p.nf_share = tu.nf_share;
+      p.policy = policy;
+    }
+    __syncthreads();
+    solve_body(p, p, grp, smem);
     if (*(volatile int*)err != 0) return;
     if (rank == 0 && threadIdx.x == 0) {
       const int e = (int)ldcg_u32(reinterpret_cast<const uint32_t*>(&p.ws.ctl->err));
