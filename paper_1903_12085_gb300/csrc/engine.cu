@@ -907,13 +907,16 @@ __device__ __noinline__ bool phase_relax(const SolveParams& p, const Grp& grp, c
   int dfar = 0;
   const unsigned int nwarps = nthr >> 5;
   const uint64_t gwarps = (uint64_t)grp.size * nwarps;
-  // the owner marks of the warp's first tile are loaded together with the
-  // list's size (unused if the tile lies past the phase's edges)
+  // The warp's tiles are software-pipelined: while tile i's slot
+  // reservations (next queue, bucket lists) are in flight, tile i+1's relax
+  // entries are staged and its edge loads issued; tile i+1's owner marks are
+  // loaded before tile i is relaxed.
   const uint64_t tile0 = (uint64_t)grp.rank * nwarps + warp;
-  uint32_t own0 = 0, own1 = 0;
-  if (w.tile_owner && tile0 + 1 < g.m / kTile + 2) {
-    own0 = ldcg_u32(&w.tile_owner[tile0]);
-    own1 = ldcg_u32(&w.tile_owner[tile0 + 1]);
+  const uint64_t owner_len = g.m / kTile + 2;  // length of the tile-owner array
+  uint32_t mlo = 0, mhi = 0;  // owner marks of the next tile to stage
+  if (w.tile_owner && tile0 + 1 < owner_len) {
+    mlo = ldcg_u32(&w.tile_owner[tile0]);
+    mhi = ldcg_u32(&w.tile_owner[tile0 + 1]);
   }
   const unsigned long long packed = ldcg_u64(&S0->relax_packed);
   const uint32_t nS = (uint32_t)(packed >> 32);
@@ -928,15 +931,20 @@ __device__ __noinline__ bool phase_relax(const SolveParams& p, const Grp& grp, c
     for (uint32_t j = lane; j < kNfRing; j += 32) wh[j] = 0;
     __syncwarp();
   }
-  for (uint64_t tile = tile0; tile * kTile < E; tile += gwarps) {
-    const uint32_t e0 = (uint32_t)(tile * kTile);
+  // Front half of tile t: stage the relax-list entries overlapping it in the
+  // warp's slice, find each edge's owner entry (ownp: 8 bits per item, the
+  // entry's index in the slice) and issue the edge loads.
+  uint2 ed[kRelaxItems];
+  uint32_t ownp = 0, valid = 0;
+  auto front = [&](uint64_t t) {
+    const uint32_t e0 = (uint32_t)(t * kTile);
     const uint32_t e1 = (uint64_t)e0 + kTile < E ? e0 + kTile : E;
     uint32_t lo = 0, hi = nS - 1;
     if (w.tile_owner) {
       // entries lo .. hi intersect the tile (hi may start just past it, and is
       // then dropped by the kTile cap below: the per-edge search never picks it)
-      lo = tile == tile0 ? own0 : ldcg_u32(&w.tile_owner[tile]);
-      if (e1 < E) hi = tile == tile0 ? own1 : ldcg_u32(&w.tile_owner[tile + 1]);
+      lo = mlo;
+      if (e1 < E) hi = mhi;
     } else if (!(e0 == 0 && e1 == E)) {
       lo = warp_upper_bound_sp(w.sp, nS, e0) - 1;
       hi = warp_upper_bound_sp(w.sp, nS, e1 - 1) - 1;
@@ -949,14 +957,12 @@ __device__ __noinline__ bool phase_relax(const SolveParams& p, const Grp& grp, c
       s_d[j] = e.d;
     }
     __syncwarp();
-    uint2 ed[kRelaxItems];
-    uint32_t own[kRelaxItems];  // owner entry in the staged slice (its d is read again at the relaxation)
-    uint32_t valid = 0;
+    ownp = 0;
+    valid = 0;
 #pragma unroll
     for (int it = 0; it < kRelaxItems; ++it) {
       const uint32_t e = e0 + it * 32 + lane;
       ed[it] = make_uint2(0, 0);
-      own[it] = 0;
       if (e < e1) {
         uint32_t a = 0, b = cnt;  // owner = last j with s_base[j] <= e
         while (b - a > 1) {
@@ -964,64 +970,118 @@ __device__ __noinline__ bool phase_relax(const SolveParams& p, const Grp& grp, c
           if (s_base[mid] <= e) a = mid; else b = mid;
         }
         ed[it] = __ldg(&g.edges[s_row[a] + (e - s_base[a])]);
-        own[it] = a;
+        ownp |= a << (8 * it);
         valid |= 1u << it;
       }
     }
+  };
+  static_assert(kTile <= 256 && kRelaxItems <= 4, "owner indices packed 8 bits per item");
+  if (tile0 * kTile < E) front(tile0);
+  for (uint64_t tile = tile0; tile * kTile < E;) {
+    const uint64_t next = tile + gwarps;
+    const bool has_next = next * kTile < E;
+    if (has_next && w.tile_owner && next + 1 < owner_len) {
+      mlo = ldcg_u32(&w.tile_owner[next]);
+      mhi = ldcg_u32(&w.tile_owner[next + 1]);
+    }
+    // ---- back half of this tile: target records, relaxations
     VRec rt[kRelaxItems];
 #pragma unroll
     for (int it = 0; it < kRelaxItems; ++it)
       if ((valid >> it) & 1u) rt[it] = ldcg_vrec(&w.vrec[ed[it].x]);
     uint32_t fmask = 0;
-    uint32_t app[kRelaxItems];
+    uint32_t app[kRelaxItems], tv[kRelaxItems];
 #pragma unroll
     for (int it = 0; it < kRelaxItems; ++it) {
       app[it] = kNoBucket;
+      tv[it] = ed[it].x;
       if ((valid >> it) & 1u) {
         bool fresh = false;
-        relax_edge_rec<kNF>(p, md, ed[it].x, ed[it].y, s_d[own[it]], rt[it], nv, pd, po, fresh, dfar, app[it]);
+        relax_edge_rec<kNF>(p, md, ed[it].x, ed[it].y, s_d[(ownp >> (8 * it)) & 0xFFu], rt[it], nv, pd, po, fresh,
+                            dfar, app[it]);
         if (fresh) fmask |= 1u << it;
       }
     }
-    if (kNF) {
-      uint32_t tv[kRelaxItems];
-#pragma unroll
-      for (int it = 0; it < kRelaxItems; ++it) tv[it] = ed[it].x;
-      nf_list_append_warp<kRelaxItems>(nv, app, tv, wh);
-    }
-    // vertices new to F: one atomic per tile (APPROX also lists them for the
-    // next phase's bookkeeping)
-    uint32_t fb[kRelaxItems];
+    // reservations, issued now and consumed after the next tile's front half:
+    // next-queue slots (one atomic per tile) ...
     uint32_t nfr = 0;
 #pragma unroll
-    for (int it = 0; it < kRelaxItems; ++it) {
-      fb[it] = __ballot_sync(0xFFFFFFFFu, (fmask >> it) & 1u);
-      nfr += __popc(fb[it]);
+    for (int it = 0; it < kRelaxItems; ++it) nfr += __popc(__ballot_sync(0xFFFFFFFFu, (fmask >> it) & 1u));
+    unsigned int fslot = 0, xslot = 0;
+    if (nfr && lane == 0) {
+      fslot = atomicAdd(&S1->qcount, nfr);
+      if (md.approx) xslot = atomicAdd(&S1->fresh_count, nfr);
     }
-    if (nfr) {
-      unsigned int fslot = 0, xslot = 0;
-      if (lane == 0) {
-        fslot = atomicAdd(&S1->qcount, nfr);
-        if (md.approx) xslot = atomicAdd(&S1->fresh_count, nfr);
+    // ... and bucket-list ranges: ranks within the warp per ring slot
+    // (shared-memory atomics), then one global atomicAdd per slot used, its
+    // result kept by the lane of that slot (slot j: lane j & 31, word j >> 5)
+    uint32_t rankp = 0, lmask = 0, unl = kInf32;
+    unsigned int lb0 = 0, lb1 = 0;
+    bool any_far = false;
+    if (kNF) {
+      bool mine = false;
+#pragma unroll
+      for (int it = 0; it < kRelaxItems; ++it) mine |= app[it] != kNoBucket;
+      any_far = __any_sync(0xFFFFFFFFu, mine);
+    }
+    if (any_far) {
+#pragma unroll
+      for (int it = 0; it < kRelaxItems; ++it) {
+        const bool want = app[it] != kNoBucket;
+        const bool listed = want && app[it] <= nv.cursor + kNfRing;
+        if (want && !listed) unl = min(unl, app[it]);
+        if (listed) {
+          rankp |= atomicAdd(&wh[app[it] & (kNfRing - 1)], 1u) << (8 * it);
+          lmask |= 1u << it;
+        }
       }
+      __syncwarp();
+      const uint32_t c0 = wh[lane], c1 = wh[lane + 32];
+      if (c0) lb0 = atomicAdd(&nv.cnt[lane], c0);
+      if (c1) lb1 = atomicAdd(&nv.cnt[lane + 32], c1);
+      wh[lane] = 0;
+      wh[lane + 32] = 0;
+    }
+    static_assert(kNfRing == 64, "two ring slots per lane");
+    __syncwarp();  // the slice is read; the next tile may overwrite it
+    // ---- front half of the next tile
+    if (has_next) front(next);
+    // ---- this tile's appends
+    if (nfr) {
       fslot = __shfl_sync(0xFFFFFFFFu, fslot, 0);
       xslot = __shfl_sync(0xFFFFFFFFu, xslot, 0);
 #pragma unroll
       for (int it = 0; it < kRelaxItems; ++it) {
+        const unsigned int fb = __ballot_sync(0xFFFFFFFFu, (fmask >> it) & 1u);
         if ((fmask >> it) & 1u) {
-          const uint32_t off = __popc(fb[it] & lt);
-          if (fslot + off < n) Qn[fslot + off] = ed[it].x;
+          const uint32_t off = __popc(fb & lt);
+          if (fslot + off < n) Qn[fslot + off] = tv[it];
           else atomicCAS(&ctl->err, 0, (int)SSSP_ERR_INTERNAL);
           if (md.approx) {
-            if (xslot + off < n) w.fresh[xslot + off] = ed[it].x;
+            if (xslot + off < n) w.fresh[xslot + off] = tv[it];
             else atomicCAS(&ctl->err, 0, (int)SSSP_ERR_INTERNAL);
           }
         }
-        fslot += __popc(fb[it]);
-        xslot += __popc(fb[it]);
+        fslot += __popc(fb);
+        xslot += __popc(fb);
       }
     }
-    __syncwarp();  // the staged entries are read before the next tile overwrites them
+    if (any_far) {
+#pragma unroll
+      for (int it = 0; it < kRelaxItems; ++it) {
+        const uint32_t slot = app[it] & (kNfRing - 1);
+        const unsigned int b0 = __shfl_sync(0xFFFFFFFFu, lb0, slot & 31);
+        const unsigned int b1 = __shfl_sync(0xFFFFFFFFu, lb1, slot & 31);
+        if ((lmask >> it) & 1u) {
+          const uint32_t pos = (slot < 32 ? b0 : b1) + ((rankp >> (8 * it)) & 0xFFu);
+          if (pos < nv.cap) nv.lists[(uint64_t)slot * nv.cap + pos] = tv[it];
+          else unl = min(unl, app[it]);
+        }
+      }
+      unl = __reduce_min_sync(0xFFFFFFFFu, unl);
+      if (lane == 0 && unl != kInf32) atomicMin(nv.beyond, unl);
+    }
+    tile = next;
   }
   if (md.fused) block_min2_to_global(pd, po, &S1->min_d, md.use_out ? &S1->min_out : nullptr, sh.red);
   if (kNF) {  // far-part count: one atomic per block (the barrier above orders scratch reuse)
@@ -1189,13 +1249,14 @@ __device__ __forceinline__ uint64_t solo_episode(const SolveParams& p, const Mod
 
   const uint32_t cap = p.solo_max < kSoloCap ? p.solo_max : kSoloCap;
   // counters of the previous phase (policy features)
-  uint64_t e_prev = (uint32_t)ldcg_u64(&ctl->slot[(k + 3) % 4].relax_packed);
-  uint64_t s_prev = ldcg_u32(&ctl->slot[(k + 3) % 4].settled_now);
-  uint64_t f_prev = ldcg_u32(&ctl->slot[(k + 3) % 4].fsize);
+  uint32_t e_prev = (uint32_t)ldcg_u64(&ctl->slot[(k + 3) % 4].relax_packed);
+  uint32_t s_prev = ldcg_u32(&ctl->slot[(k + 3) % 4].settled_now);
+  uint32_t f_prev = ldcg_u32(&ctl->slot[(k + 3) % 4].fsize);
   uint32_t nF = ldcg_u32(&ctl->slot[k % 4].qcount);
   const bool kNF = nv.bound != kNoBound;
   uint32_t far = kNF ? ldcg_u32(&ctl->far_count) : 0u;  // far part of F (not in the queues)
-  Stats st = st_shared;  // thread 0's running counters, in registers for the episode
+  Stats& st = st_shared;  // thread 0's running counters
+  __shared__ unsigned long long s_t0, s_tsel;  // thread 0's trace stamps
   Arm arm{false, false, -1};
   unsigned int since_pick = 0;
   unsigned long long minD = min(ldcg_u64(&ctl->slot[k % 4].min_d), ldcg_u64(&ctl->slot[k % 4].a_min_d));
@@ -1225,8 +1286,7 @@ __device__ __forceinline__ uint64_t solo_episode(const SolveParams& p, const Mod
     since_pick = (since_pick + 1) & 7u;
     const bool in_dyn = md.use_in && arm.in_simple && w.cur_in != nullptr;
     const uint32_t fs = nF + far;  // |F| at the start of the phase
-    unsigned long long t0 = 0, t_sel = 0;
-    if (tid == 0 && w.trace) t0 = globaltimer_ns();
+    if (tid == 0 && w.trace) s_t0 = globaltimer_ns();
     // ---- B1: load the records of this thread's fringe entries (all in flight at once)
     constexpr int kIt = kSoloCap / kThreads;
     VRec r[kIt];
@@ -1385,12 +1445,11 @@ __device__ __forceinline__ uint64_t solo_episode(const SolveParams& p, const Mod
         S0->relax_packed = packed;
         S0->settled_now = s_settled[pb];
         S0->arm = arm_code(arm, true) | nf_code;
-        S0->t_start = t0;
+        S0->t_start = s_t0;
         S0->t_select = globaltimer_ns();
         S1->qcount = kept;
         S1->min_d = s_thr_d[pb];
         S1->min_out = s_thr_o[pb];
-        st_shared = st;
       }
       __threadfence();
       __syncthreads();
@@ -1398,7 +1457,7 @@ __device__ __forceinline__ uint64_t solo_episode(const SolveParams& p, const Mod
       return k;
     }
     // ---- C: relax
-    if (tid == 0 && w.trace) t_sel = globaltimer_ns();
+    if (tid == 0 && w.trace) s_tsel = globaltimer_ns();
     pd = kInf64;
     po = kInf64;
     int dfar = 0;
@@ -1433,10 +1492,10 @@ __device__ __forceinline__ uint64_t solo_episode(const SolveParams& p, const Mod
         if (md.use_in) c = (c & ~(uint32_t)(SSSP_IN_STATIC | SSSP_IN_SIMPLE)) | (in_dyn ? SSSP_IN_SIMPLE : SSSP_IN_STATIC);
         r.criterion = c;
         r.arm = arm_code(arm, true) | nf_code;
-        r.t_start_ns = t0;
+        r.t_start_ns = s_t0;
         r.t_end_ns = globaltimer_ns();
         r.queued = nF;
-        r.select_ns = (uint32_t)(t_sel - t0);
+        r.select_ns = (uint32_t)(s_tsel - s_t0);
         w.trace[k - 1] = r;
       }
     }
@@ -1461,7 +1520,6 @@ __device__ __forceinline__ uint64_t solo_episode(const SolveParams& p, const Mod
     for (uint32_t i = tid; i < ns; i += nthr) gq[i] = sq[i];
   }
   if (tid == 0) {
-    st_shared = st;
     PhaseSlot* S0 = &ctl->slot[k % 4];
     reset_slot(S0);
     reset_slot(&ctl->slot[(k + 1) % 4]);
