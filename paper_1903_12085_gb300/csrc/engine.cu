@@ -199,7 +199,7 @@ struct Shared {
   unsigned long long* s_d;    // kWarps * kTile
   uint32_t* s_range;          // 2
   uint32_t* scan;             // 34
-  uint32_t* whist;            // kWarps * 2 * kNfRing: per-warp bucket counts and list offsets
+  uint32_t* whist;            // kWarps * kNfRing: per-warp bucket-list counts of a relax tile
 };
 
 __device__ __forceinline__ Shared carve(unsigned char* smem) {
@@ -420,49 +420,6 @@ __device__ __forceinline__ void nf_list_append_n(const NfView& nv, const uint32_
       else unl = min(unl, b[i]);
     }
   }
-  unl = __reduce_min_sync(0xFFFFFFFFu, unl);
-  if (lane == 0 && unl != kInf32) atomicMin(nv.beyond, unl);
-}
-
-// nf_list_append for N items per lane, aggregated per warp: every item takes
-// its rank within the warp's count for its ring slot (shared-memory atomics in
-// `wh`, the warp's 2 * kNfRing words, zero on entry and on return), then one
-// global atomicAdd per slot the warp uses reserves the slot's list range.
-template <int N>
-__device__ __forceinline__ void nf_list_append_warp(const NfView& nv, const uint32_t (&b)[N], const uint32_t (&v)[N],
-                                                    uint32_t* wh) {
-  bool any = false;
-#pragma unroll
-  for (int i = 0; i < N; ++i) any |= b[i] != kNoBucket;
-  if (!__any_sync(0xFFFFFFFFu, any)) return;
-  const unsigned int lane = threadIdx.x & 31;
-  uint32_t slot[N], rank[N];
-  uint32_t unl = kInf32;
-#pragma unroll
-  for (int i = 0; i < N; ++i) {
-    const bool want = b[i] != kNoBucket;
-    const bool listed = want && b[i] <= nv.cursor + kNfRing;
-    if (want && !listed) unl = min(unl, b[i]);
-    slot[i] = listed ? (b[i] & (kNfRing - 1)) : kInf32;
-    rank[i] = listed ? atomicAdd(&wh[slot[i]], 1u) : 0u;
-  }
-  __syncwarp();
-  for (uint32_t j = lane; j < kNfRing; j += 32) {
-    const uint32_t c = wh[j];
-    if (c) wh[kNfRing + j] = atomicAdd(&nv.cnt[j], c);
-  }
-  __syncwarp();
-#pragma unroll
-  for (int i = 0; i < N; ++i) {
-    if (slot[i] != kInf32) {
-      const uint32_t pos = wh[kNfRing + slot[i]] + rank[i];
-      if (pos < nv.cap) nv.lists[(uint64_t)slot[i] * nv.cap + pos] = v[i];
-      else unl = min(unl, b[i]);
-    }
-  }
-  __syncwarp();
-  for (uint32_t j = lane; j < kNfRing; j += 32) wh[j] = 0;
-  __syncwarp();
   unl = __reduce_min_sync(0xFFFFFFFFu, unl);
   if (lane == 0 && unl != kInf32) atomicMin(nv.beyond, unl);
 }
@@ -926,7 +883,7 @@ __device__ __noinline__ bool phase_relax(const SolveParams& p, const Grp& grp, c
   uint32_t* s_base = sh.s_base + warp * kTile;
   uint32_t* s_row = sh.s_row + warp * kTile;
   unsigned long long* s_d = sh.s_d + warp * kTile;
-  uint32_t* wh = sh.whist + warp * 2 * kNfRing;
+  uint32_t* wh = sh.whist + warp * kNfRing;
   if (kNF) {
     for (uint32_t j = lane; j < kNfRing; j += 32) wh[j] = 0;
     __syncwarp();

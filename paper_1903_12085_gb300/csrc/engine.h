@@ -26,7 +26,7 @@ constexpr uint32_t kNearFarShareDefault = 8;       // ... and fringe share of n,
 constexpr size_t kGridSmem = 66 * sizeof(unsigned long long)                                         // reduction scratch, bases
                              + kWarps * kTile * (2 * sizeof(uint32_t) + sizeof(unsigned long long))  // relax tiles
                              + 36 * sizeof(uint32_t)                                                   // range, scan
-                             + kWarps * 2 * kNfRing * sizeof(uint32_t);                                // bucket counts
+                             + kWarps * kNfRing * sizeof(uint32_t);                                    // bucket counts
 constexpr size_t kSoloSmem = 64 * sizeof(unsigned long long)                       // reduction scratch
                              + 2 * kSoloCap * sizeof(uint32_t)                     // two queues
                              + kSoloCap * (2 * sizeof(uint32_t) + sizeof(unsigned long long))  // relax list
