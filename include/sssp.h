@@ -122,8 +122,10 @@ typedef struct sssp_graph sssp_graph;
  * edges into v; with SSSP_GRAPH_REVERSE the in-edge CSR is built and its
  * rows sorted by (cost, source).  The caller keeps ownership of its arrays;
  * the handle owns its device copies.  Invalid input -> SSSP_ERR_INVALID_ARG
- * with nothing allocated (host inputs are checked on the host, device inputs
- * by a device pass).  *out is set only on success.
+ * with nothing left allocated: the ends of host row_offsets are checked
+ * before any allocation, everything else by one device pass over the copied
+ * arrays (host and device inputs alike), after which the call frees what it
+ * took.  *out is set only on success.
  */
 sssp_status sssp_graph_create(uint32_t n, uint64_t m, const uint64_t* row_offsets,
                               const uint32_t* col_idx, const uint32_t* weights,
