@@ -157,3 +157,29 @@ def test_device_memory_cap_refuses_before_cudamalloc():
         assert sp.device_memory_in_use() == base
     finally:
         sp.set_device_memory_limit(0)
+
+
+def test_graph_create_checks_host_offset_ends_before_any_cuda_call():
+    """Host CSR: row_offsets[0] != 0, row_offsets[n] != m, and the decreasing
+    offsets of an edgeless graph are refused with SSSP_ERR_INVALID_ARG before
+    any allocation or CUDA call (so this needs no GPU); the per-edge checks
+    run on the device after the copy."""
+    import ctypes
+
+    import numpy as np
+
+    import paper_1903_12085_gb300 as sp
+
+    L = sp.lib()
+    col, w = np.array([1, 2], np.uint32), np.array([5, 6], np.uint32)
+    cases = [(3, 2, np.array([1, 1, 2, 2], np.uint64), "row_offsets[0]"),
+             (3, 2, np.array([0, 1, 2, 3], np.uint64), "row_offsets[n]"),
+             (2, 0, np.array([0, 1, 0], np.uint64), "decrease")]
+    base = sp.device_memory_in_use()
+    for n, m, ro, msg in cases:
+        h = ctypes.c_void_p()
+        st = L.sssp_graph_create(n, m, sp._ptr(ro), sp._ptr(col), sp._ptr(w), 0, 0, None, ctypes.byref(h))
+        assert st == 1, msg
+        assert msg.encode() in L.sssp_last_error()
+        assert h.value is None
+    assert sp.device_memory_in_use() == base
