@@ -80,7 +80,7 @@ def parse():
 # workload name and criterion, with a hash of the engine sources the capture ran
 # on: once the kernel changes the figure no longer applies and is reported null.
 MEASURED_TRAFFIC = {
-    # profiles/dram_batch_gnm2p24.md: one timed launch of the default step
+    # one timed launch of the default step (8 solves of G(2^24, 2^28), 152 blocks)
     ("gnm_n16777216_m268435456", "learned", "k_solve_batch"): (471704877312 + 42709658368, "5d86847cefe8b298"),
 }
 ENGINE_SOURCES = ("engine.cu", "engine.h", "common.cuh", "policy.cuh")
